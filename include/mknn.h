@@ -1,0 +1,235 @@
+/*
+ * mknn.h - C ABI of the GB300 Manifold k-NN query library.
+ *
+ * The library answers exact k-nearest-neighbour queries against a point
+ * set P = {p_1..p_n} ordered by insertion ("birth") time, optionally
+ * restricted to a prefix P_{1:m} (Manifold k-NN, Sec. 3-4). A host-side
+ * builder makes the successor table once (Sec. 3: j is in L_i iff p_j is a
+ * Delaunay neighbour of p_i in DT(P_{1:j})); queries then run on the GPU:
+ * the successor-list descent of Algorithm 1 followed by the expansion of
+ * Algorithm 2, whose correctness is Theorem 1.
+ *
+ * Conventions
+ *  - Ranks are 0-based insertion ranks: the paper's p_i is rank i-1.
+ *    Results are ranks; mknn_cloud_order maps ranks to input indices.
+ *  - Squared Euclidean distances, float32 coordinates.
+ *  - Ties are broken by the lower rank (Eq. 2 keeps the earlier site).
+ *  - Every function returns a status; none throws. mknn_last_error()
+ *    gives a message for the calling thread's last failure.
+ *  - Pointers documented as "device" must be CUDA device memory of the
+ *    current device (e.g. a torch tensor's data_ptr()); "host" pointers
+ *    are ordinary host memory (pinned memory makes copies faster).
+ *  - Streams are CUDA stream handles (cudaStream_t); NULL is the legacy
+ *    default stream. Device work is asynchronous on the given stream.
+ *  - Thread safety: distinct clouds may be used from distinct threads; a
+ *    cloud may be queried concurrently, but mknn_cloud_free must not race
+ *    with its use.
+ */
+#ifndef MKNN_H_
+#define MKNN_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* mknn_stream_t; /* same type as cudaStream_t */
+
+typedef enum {
+  MKNN_OK = 0,
+  MKNN_EINVAL = 1,      /* bad argument (k, m, sizes, NULL pointer, NaN coords) */
+  MKNN_ENOMEM = 2,      /* host or device allocation failed */
+  MKNN_ECUDA = 3,       /* a CUDA runtime call failed */
+  MKNN_EBUSY = 4,       /* object in use (e.g. cloud referenced by a server) */
+  MKNN_ETIMEOUT = 5,    /* a bounded wait expired */
+  MKNN_EDEGENERATE = 6, /* input too degenerate to build (all points coplanar) */
+  MKNN_EIO = 7          /* file could not be read or written, or bad format */
+} mknn_status;
+
+/* Largest k accepted by the query entry points. */
+#define MKNN_MAX_K 64
+
+typedef struct mknn_cloud mknn_cloud;
+
+/* Message describing the calling thread's most recent failure ("" if none).
+ * The pointer stays valid until the next library call on the thread. */
+const char* mknn_last_error(void);
+
+/* ------------------------------------------------------------------ build
+ * mknn_build: the successor table of Sec. 3, made by an incremental 3D
+ * Delaunay triangulation with exact predicates on the host.
+ *   xyz    host, n*3 float32, input order (row i = point i).
+ *   n      number of points, 1 <= n < 2^31 - 16.
+ *   order  host int64[n] or NULL. order[r] = input index of the point
+ *          inserted at rank r (a permutation of 0..n-1). NULL = identity.
+ *   opts   NULL for defaults.
+ *   out    receives a new cloud owned by the caller (mknn_cloud_free).
+ * Errors: EINVAL (NULL, n out of range, non-finite coordinate, order not a
+ * permutation), EDEGENERATE (all points coplanar and n > 4096), ENOMEM.
+ * The caller's arrays are copied; they can be freed on return. Nothing is
+ * placed on the device until mknn_cloud_upload. Thread-safe for distinct
+ * outputs (builds of several clouds may run in parallel threads). */
+typedef struct {
+  int32_t keep_tets; /* nonzero: keep the final tetrahedra (mknn_cloud_tets) */
+  int32_t reserved[7];
+} mknn_build_opts;
+
+mknn_status mknn_build(const float* xyz, int64_t n, const int64_t* order,
+                       const mknn_build_opts* opts, mknn_cloud** out);
+
+/* mknn_cloud_from_table: a cloud from an explicit successor table instead
+ * of the builder. Any table whose rows are supersets of the true successor
+ * lists gives exact results (extra entries are extra candidates), e.g. the
+ * complete table L_i = {i+1..n-1}.
+ *   xyz_ranked host float32[n*3], rank order.
+ *   rowp       host int64[n+1], rowp[0] = 0, nondecreasing, rowp[n] = E.
+ *   succ       host int32[E]; row i = succ[rowp[i]..rowp[i+1]), strictly
+ *              ascending, every entry in (i, n).
+ * Errors: EINVAL (shape or ordering violated, E >= 2^31), ENOMEM. */
+mknn_status mknn_cloud_from_table(const float* xyz_ranked, int64_t n, const int64_t* rowp,
+                                  const int32_t* succ, mknn_cloud** out);
+
+/* Copies coordinates (as float4 x,y,z,0 in rank order) and the CSR table to
+ * the current device. Idempotent; synchronous with respect to the host
+ * (the copies complete before return). Device bytes: 16 n + 4 (n+1) + 4 E
+ * plus a few words of status. Errors: ENOMEM, ECUDA. */
+mknn_status mknn_cloud_upload(mknn_cloud* cloud, mknn_stream_t stream);
+
+/* Releases device memory of the cloud (keeps the host copy). */
+mknn_status mknn_cloud_release_device(mknn_cloud* cloud);
+
+/* Frees the cloud (host and device). EBUSY if a server still holds it. */
+mknn_status mknn_cloud_free(mknn_cloud* cloud);
+
+/* Sizes: n, E (total successor entries) and device bytes (0 if not
+ * uploaded). Any output pointer may be NULL. */
+mknn_status mknn_cloud_info(const mknn_cloud* cloud, int64_t* n, int64_t* E, size_t* dev_bytes);
+
+/* order_out host int64[n]: rank -> input index. */
+mknn_status mknn_cloud_order(const mknn_cloud* cloud, int64_t* order_out);
+
+/* Copies the table to host arrays: xyz_ranked float[3n], rowp int64[n+1],
+ * succ int32[E]. Any pointer may be NULL to skip it. */
+mknn_status mknn_cloud_table(const mknn_cloud* cloud, float* xyz_ranked, int64_t* rowp,
+                             int32_t* succ);
+
+/* Build statistics. */
+typedef struct {
+  int64_t n, entries, duplicates, degenerate_prefix, tets_final;
+  int64_t walk_steps, conflict_tests;
+  int64_t orient_calls, orient_exact, insphere_calls, insphere_exact;
+  double build_seconds;
+} mknn_build_stats;
+mknn_status mknn_cloud_stats(const mknn_cloud* cloud, mknn_build_stats* out);
+
+/* Final finite tetrahedra (rank quadruples, positively oriented) of a cloud
+ * built with keep_tets. tets may be NULL to query *count only. */
+mknn_status mknn_cloud_tets(const mknn_cloud* cloud, int32_t* tets, int64_t* count);
+
+/* Checkpoint: versioned binary file with n, E, coordinates (rank order),
+ * rank order and the CSR table. load gives a host-only cloud. */
+mknn_status mknn_cloud_save(const mknn_cloud* cloud, const char* path);
+mknn_status mknn_cloud_load(const char* path, mknn_cloud** out);
+
+/* ------------------------------------------------------------------ query
+ * mknn_knn: exact k-NN for a batch of queries (Algorithms 1 and 2, with the
+ * prefix bound of Sec. 4.2), one query per group of lanes.
+ *   cloud     uploaded cloud.
+ *   q         device float32, nq rows of q_stride floats (x, y, z first).
+ *   nq        number of queries, 0 <= nq < 2^31.
+ *   q_stride  floats per query row, >= 3 (3 = packed xyz, 4 = float4).
+ *   k         1 <= k <= MKNN_MAX_K.
+ *   m         device int32[nq] per-query prefix bounds, or NULL.
+ *   m_scalar  used when m is NULL: 0 means n, otherwise 1 <= m_scalar <= n.
+ *   out_idx   device int32[nq*k]: ranks in [0, m), row-major per query.
+ *   out_d2    device float32[nq*k]: squared distances (float32 arithmetic).
+ *   stream    CUDA stream.
+ * Each row is sorted by (distance, rank). If min(k, m) < k the row is padded
+ * with (-1, +inf). A per-query m outside [1, n] yields a padded row and
+ * sets the cloud's error flag (mknn_cloud_check). Results equal the float64
+ * brute force up to the order of distances that differ by less than about
+ * 3e-7 relative (float32 rounding). Errors: EINVAL, ECUDA. */
+mknn_status mknn_knn(const mknn_cloud* cloud, const float* q, int64_t nq, int32_t q_stride,
+                     int32_t k, const int32_t* m, int32_t m_scalar, int32_t* out_idx,
+                     float* out_d2, mknn_stream_t stream);
+
+/* Tuning knobs of one query launch; zero-initialise for defaults. */
+typedef struct {
+  int32_t lanes;        /* lanes per query: 0 = default, or 4, 8, 16, 32 */
+  int32_t sort;         /* query locality sort: 0 = default, 1 = on, -1 = off */
+  int32_t blocks_per_sm;/* 0 = as many as fit */
+  int32_t* counters;    /* device int32[4*nq] or NULL: per query rows opened,
+                           successor entries read, coordinates read and
+                           transition sites (descent moves + 1) */
+  void* workspace;      /* device scratch or NULL (library-managed) */
+  size_t workspace_bytes;
+  const int32_t* order; /* device int32[nq] processing order (e.g. from
+                           mknn_query_order) or NULL; overrides sort */
+  int32_t reserved[4];
+} mknn_knn_opts;
+
+/* Locality order of a query batch, the one mknn_knn_ex applies when sort
+ * is on: queries counting-sorted by the Morton index of their cell in a
+ * 64^3 grid over the cloud's bounding box. Changes only the processing
+ * order, never a result.
+ *   perm_out   device int32[nq]: query indices in processing order.
+ *   workspace  device scratch of mknn_query_order_workspace_size(nq) bytes,
+ *              or NULL (library-managed, grown on demand).
+ * Errors: EINVAL, ENOMEM, ECUDA. */
+size_t mknn_query_order_workspace_size(int64_t nq);
+mknn_status mknn_query_order(const mknn_cloud* cloud, const float* q, int64_t nq, int32_t q_stride,
+                             int32_t* perm_out, void* workspace, size_t workspace_bytes,
+                             mknn_stream_t stream);
+
+/* Scratch bytes mknn_knn_ex needs for nq queries with the given options. */
+size_t mknn_knn_workspace_size(int64_t nq, const mknn_knn_opts* opts);
+
+/* mknn_knn with explicit options (opts may be NULL). A caller workspace of
+ * at least mknn_knn_workspace_size bytes avoids library allocations. */
+mknn_status mknn_knn_ex(const mknn_cloud* cloud, const float* q, int64_t nq, int32_t q_stride,
+                        int32_t k, const int32_t* m, int32_t m_scalar, int32_t* out_idx,
+                        float* out_d2, const mknn_knn_opts* opts, mknn_stream_t stream);
+
+/* End-to-end form with HOST buffers: copies queries (and m) to the device,
+ * runs the query, copies results back, in chunks pipelined over two
+ * streams. Returns after the results are in the host buffers.
+ *   q host float32 [nq*q_stride]; m host int32[nq] or NULL;
+ *   out_idx host int32[nq*k]; out_d2 host float32[nq*k].
+ * Pinned host memory is used directly; pageable memory works but is
+ * slower. Errors: EINVAL, ENOMEM, ECUDA. */
+mknn_status mknn_knn_host(const mknn_cloud* cloud, const float* q, int64_t nq, int32_t q_stride,
+                          int32_t k, const int32_t* m, int32_t m_scalar, int32_t* out_idx,
+                          float* out_d2, mknn_stream_t stream);
+
+/* Reads and clears the cloud's device error flags (synchronises the
+ * device). Bit 0: a per-query m was outside [1, n]. */
+mknn_status mknn_cloud_check(const mknn_cloud* cloud, int32_t* flags);
+
+/* ------------------------------------------------------------ diagnostics
+ * Exact geometric predicates used by the builder (float32 inputs):
+ * orient3d = sign det[b-a; c-a; d-a]; insphere = +1 inside, 0 on, -1
+ * outside the sphere through a, b, c, d (positively oriented). */
+int32_t mknn_orient3d(const float* a, const float* b, const float* c, const float* d);
+int32_t mknn_insphere(const float* a, const float* b, const float* c, const float* d,
+                      const float* e);
+/* Same predicates without the floating-point filter (exact stage only). */
+int32_t mknn_orient3d_exact(const float* a, const float* b, const float* c, const float* d);
+int32_t mknn_insphere_exact(const float* a, const float* b, const float* c, const float* d,
+                            const float* e);
+
+/* Brute-force check of a cloud built with keep_tets (O(tets * n), for tests
+ * on small inputs): *bad_orient = tetrahedra that are not positively
+ * oriented, *bad_sphere = (tetrahedron, site) pairs with the site strictly
+ * inside the circumsphere. Both 0 for a valid Delaunay triangulation. */
+mknn_status mknn_cloud_validate(const mknn_cloud* cloud, int64_t* bad_orient, int64_t* bad_sphere);
+
+/* Library version string. */
+const char* mknn_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MKNN_H_ */

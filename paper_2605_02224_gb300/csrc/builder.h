@@ -1,0 +1,44 @@
+// Host-side successor-table builder (Sec. 3; construction as in Sec. 2.2).
+//
+// Sites are inserted in rank order into an incremental 3D Delaunay
+// triangulation (Bowyer-Watson). When p_j is inserted, j is appended to
+// the successor list L_i of every Delaunay neighbour p_i of p_j in
+// DT(P_{1:j}) (the vertices of the conflict cavity's boundary). Lists are
+// therefore ascending. Ranks are 0-based.
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+namespace mknn {
+
+struct BuildStats {
+  int64_t n = 0;
+  int64_t entries = 0;          // E = sum of list lengths
+  int64_t duplicates = 0;       // ranks whose coordinates repeat an earlier rank
+  int64_t degenerate_prefix = 0;  // ranks 0..j0 that start with complete lists
+  int64_t tets_final = 0;       // finite tetrahedra at the end
+  int64_t walk_steps = 0;
+  int64_t conflict_tests = 0;
+  int64_t orient_calls = 0, orient_exact = 0;
+  int64_t insphere_calls = 0, insphere_exact = 0;
+  double seconds = 0.0;
+};
+
+struct SuccessorTable {
+  std::vector<int64_t> rowp;    // n + 1
+  std::vector<int32_t> succ;    // E, each row ascending
+  std::vector<int32_t> tets;    // 4 * tets_final vertex ranks (only if requested)
+  BuildStats stats;
+};
+
+// xyz: 3 * n floats in rank order. Returns false and sets *err on failure
+// (non-finite coordinates, all points coplanar beyond the complete-table
+// limit, out of memory).
+bool build_successor_table(const float* xyz, int64_t n, bool keep_tets,
+                           SuccessorTable* out, std::string* err);
+
+// Largest all-coplanar input for which a complete table is produced.
+constexpr int64_t kMaxCoplanarComplete = 4096;
+
+}  // namespace mknn

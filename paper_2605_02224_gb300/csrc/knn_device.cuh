@@ -1,0 +1,340 @@
+// Device-side body of one k-NN query: Algorithm 1 (successor-list descent
+// collecting transition sites) then Algorithm 2 (expansion over the
+// successor lists of the nearest sites found so far), Sec. 4.
+//
+// One query is served by a group of G lanes (G = 4, 8, 16 or 32) of a
+// warp. The group reads G consecutive successor entries at a time
+// (coalesced), gathers their float4 coordinates through the read-only
+// path, and decides with warp votes.
+//
+// Candidate list N: capacity K = G * S, sorted by the key (d, rank),
+// distributed over the group: lane l, slot s holds position s * G + l. An
+// insertion counts the keys below the new one with S votes, shifts the
+// tail by one position with S shuffles per field and drops position k.
+// Bit 31 of a stored rank marks an entry whose list has been expanded.
+//
+// Readings of the paper (see the design notes for the full list):
+//  * descent: the scan of L_curr moves to the FIRST entry (lowest rank) that
+//    is strictly closer than p_curr and restarts at the head of the new
+//    list; every site moved to is inserted into N (all transition sites are
+//    candidates, Sec. 4.2);
+//  * "strictly closer" is decided in float32 with a guard band; inside the
+//    band both distances are recomputed in float64 in the oracle's order,
+//    so the descent follows the exact prefix minima of Eq. (2);
+//  * expansion: the nearest not-yet-expanded entry among the first k-1 of
+//    N is expanded until none is left (equal to Alg. 2's loop in exact
+//    arithmetic, robust to float32 reordering of near-equal distances);
+//  * prefix bound m (Sec. 4.2): rows are ascending, so a scan stops at the
+//    first entry >= m.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace mknn {
+
+constexpr uint32_t kRankMask = 0x7fffffffu;
+constexpr uint32_t kDoneBit = 0x80000000u;
+constexpr uint32_t kPadRank = 0xffffffffu;
+// |d32 - D| <= 5 * 2^-24 * D for the float32 evaluation below; the guard
+// band is three times wider than the sum of two such errors.
+constexpr float kGuard = 2e-6f;
+// Below this the float32 distance may be subnormal; decide in float64.
+constexpr float kTiny = 1e-30f;
+
+struct CloudDev {
+  const float4* __restrict__ pts;
+  const int32_t* __restrict__ rowp;
+  const int32_t* __restrict__ succ;
+  int32_t n;
+};
+
+// Squared distance in float32, fixed operation order (no reassociation).
+__device__ __forceinline__ float sqd32(float qx, float qy, float qz, float4 p) {
+  const float dx = __fsub_rn(qx, p.x);
+  const float dy = __fsub_rn(qy, p.y);
+  const float dz = __fsub_rn(qz, p.z);
+  float d = __fmul_rn(dx, dx);
+  d = __fmaf_rn(dy, dy, d);
+  d = __fmaf_rn(dz, dz, d);
+  return d;
+}
+
+// Squared distance in float64: ((dx*dx + dy*dy) + dz*dz), no fusion.
+__device__ __forceinline__ double sqd64(float qx, float qy, float qz, float px, float py,
+                                        float pz) {
+  const double dx = __dsub_rn((double)qx, (double)px);
+  const double dy = __dsub_rn((double)qy, (double)py);
+  const double dz = __dsub_rn((double)qz, (double)pz);
+  return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+}
+
+__device__ __forceinline__ bool key_lt(float da, uint32_t ra, float db, uint32_t rb) {
+  return da < db || (da == db && ra < rb);
+}
+
+template <int G>
+struct Grp {
+  uint32_t lane, base, mask;
+  __device__ __forceinline__ Grp() {
+    const uint32_t l = threadIdx.x & 31u;
+    lane = l & (G - 1);
+    base = l & ~(uint32_t)(G - 1);
+    mask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << base);
+  }
+  __device__ __forceinline__ uint32_t ballot(bool p) const {
+    const uint32_t b = __ballot_sync(mask, p);
+    return (G == 32) ? b : ((b >> base) & ((1u << G) - 1u));
+  }
+  template <class T>
+  __device__ __forceinline__ T shfl(T v, int src) const {
+    return __shfl_sync(mask, v, src, G);
+  }
+};
+
+template <int G, int S>
+struct TopK {
+  float d[S];
+  uint32_t r[S];
+  int cnt;
+  float kd;     // key of position k-1 (a pad while fewer than k entries)
+  uint32_t kr;
+};
+
+template <int G, int S>
+__device__ __forceinline__ void topk_init(TopK<G, S>& T) {
+#pragma unroll
+  for (int s = 0; s < S; ++s) {
+    T.d[s] = __int_as_float(0x7f800000);
+    T.r[s] = kPadRank;
+  }
+  T.cnt = 0;
+  T.kd = __int_as_float(0x7f800000);
+  T.kr = kRankMask;
+}
+
+// Inserts (cd, cr) unless an equal key is present; keeps k entries.
+template <int G, int S>
+__device__ __forceinline__ void topk_insert(TopK<G, S>& T, const Grp<G>& g, float cd, uint32_t cr,
+                                            int k) {
+  int less = 0;
+  bool eq = false;
+#pragma unroll
+  for (int s = 0; s < S; ++s) {
+    const uint32_t rr = T.r[s] & kRankMask;
+    less += __popc(g.ballot(key_lt(T.d[s], rr, cd, cr)));
+    eq |= (T.d[s] == cd) & (rr == cr);
+  }
+  if (g.ballot(eq) || less >= k) return;
+  const int pos = less;
+  const int src = (int)((g.lane + G - 1) & (G - 1));
+  float ud[S];
+  uint32_t ur[S];
+#pragma unroll
+  for (int s = 0; s < S; ++s) {
+    ud[s] = g.shfl(T.d[s], src);
+    ur[s] = g.shfl(T.r[s], src);
+  }
+#pragma unroll
+  for (int s = S - 1; s >= 0; --s) {
+    const int p = s * G + (int)g.lane;
+    float pd;
+    uint32_t pr;
+    if (g.lane == 0) {
+      pd = (s > 0) ? ud[s > 0 ? s - 1 : 0] : 0.f;
+      pr = (s > 0) ? ur[s > 0 ? s - 1 : 0] : 0u;
+    } else {
+      pd = ud[s];
+      pr = ur[s];
+    }
+    if (p >= k) {
+      T.d[s] = __int_as_float(0x7f800000);
+      T.r[s] = kPadRank;
+    } else if (p > pos) {
+      T.d[s] = pd;
+      T.r[s] = pr;
+    } else if (p == pos) {
+      T.d[s] = cd;
+      T.r[s] = cr;
+    }
+  }
+  T.cnt = min(T.cnt + 1, k);
+  const int kp = k - 1;
+  const int ks = kp / G, kl = kp % G;
+  float td = T.d[0];
+  uint32_t tr = T.r[0];
+#pragma unroll
+  for (int s = 1; s < S; ++s)
+    if (s == ks) {
+      td = T.d[s];
+      tr = T.r[s];
+    }
+  T.kd = g.shfl(td, kl);
+  T.kr = g.shfl(tr, kl) & kRankMask;
+}
+
+struct QueryCounters {
+  int rows, entries, coords, trans;
+};
+
+// One query by one group. m in [1, n]. Writes k results to oi / od.
+template <int G, int S, bool COUNT>
+__device__ __forceinline__ void knn_query(const CloudDev& C, const Grp<G>& g, float qx, float qy,
+                                          float qz, int k, int m, int32_t* __restrict__ oi,
+                                          float* __restrict__ od, QueryCounters& qc) {
+  const float INF = __int_as_float(0x7f800000);
+  TopK<G, S> T;
+  topk_init(T);
+
+  // ---- Algorithm 1: descent from p_1 (rank 0), collecting transition sites
+  int curr = 0;
+  float4 pc = __ldg(C.pts);
+  float dcur = sqd32(qx, qy, qz, pc);
+  topk_insert(T, g, dcur, 0u, k);
+  if (COUNT) {
+    qc.coords = 1;
+    qc.trans = 1;
+  }
+  for (;;) {
+    const int beg = __ldg(C.rowp + curr);
+    const int end = __ldg(C.rowp + curr + 1);
+    if (COUNT) qc.rows++;
+    bool moved = false;
+    for (int base = beg; base < end; base += G) {
+      const int e = base + (int)g.lane;
+      const bool valid = e < end;
+      const int s = valid ? __ldg(C.succ + e) : 0x7fffffff;
+      const bool inr = valid && s < m;
+      float4 ps = make_float4(0.f, 0.f, 0.f, 0.f);
+      float d = INF;
+      if (inr) {
+        ps = __ldg(C.pts + s);
+        d = sqd32(qx, qy, qz, ps);
+      }
+      bool sure, maybe;
+      if (dcur >= kTiny) {
+        sure = inr && d < dcur * (1.f - kGuard);
+        maybe = inr && !sure && d <= dcur * (1.f + kGuard);
+      } else {
+        sure = false;
+        maybe = inr && d <= 2.f * kTiny;
+      }
+      uint32_t closer = g.ballot(sure);
+      if (g.ballot(maybe)) {
+        bool c64 = false;
+        if (maybe) c64 = sqd64(qx, qy, qz, ps.x, ps.y, ps.z) < sqd64(qx, qy, qz, pc.x, pc.y, pc.z);
+        closer |= g.ballot(c64);
+      }
+      const uint32_t stop = g.ballot(valid && !inr);
+      if (closer) {
+        const int w = __ffs(closer) - 1;
+        if (COUNT) {
+          qc.entries += w + 1;
+          qc.coords += w + 1;
+          qc.trans++;
+        }
+        curr = g.shfl(s, w);
+        dcur = g.shfl(d, w);
+        pc.x = g.shfl(ps.x, w);
+        pc.y = g.shfl(ps.y, w);
+        pc.z = g.shfl(ps.z, w);
+        topk_insert(T, g, dcur, (uint32_t)curr, k);
+        moved = true;
+        break;
+      }
+      if (COUNT) {
+        if (stop) {
+          const int t = __ffs(stop) - 1;
+          qc.entries += t + 1;
+          qc.coords += t;
+        } else {
+          const int nv = min(G, end - base);
+          qc.entries += nv;
+          qc.coords += nv;
+        }
+      }
+      if (stop) break;
+    }
+    if (!moved) break;
+  }
+
+  // ---- Algorithm 2: expand the nearest unexpanded entry among the first k-1
+  for (;;) {
+    const int lim = min(T.cnt, k - 1);
+    int pos = -1;
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+      const int p = s * G + (int)g.lane;
+      const uint32_t b = g.ballot(p < lim && !(T.r[s] & kDoneBit));
+      if (b && pos < 0) pos = s * G + __ffs(b) - 1;
+    }
+    if (pos < 0) break;
+    const int psl = pos / G, pln = pos % G;
+    uint32_t rsel = T.r[0];
+#pragma unroll
+    for (int s = 1; s < S; ++s)
+      if (s == psl) rsel = T.r[s];
+    const int site = (int)(g.shfl(rsel, pln) & kRankMask);
+    if ((int)g.lane == pln) {
+#pragma unroll
+      for (int s = 0; s < S; ++s)
+        if (s == psl) T.r[s] |= kDoneBit;
+    }
+    const int beg = __ldg(C.rowp + site);
+    const int end = __ldg(C.rowp + site + 1);
+    if (COUNT) qc.rows++;
+    for (int base = beg; base < end; base += G) {
+      const int e = base + (int)g.lane;
+      const bool valid = e < end;
+      const int s = valid ? __ldg(C.succ + e) : 0x7fffffff;
+      const bool inr = valid && s < m;
+      float d = INF;
+      if (inr) d = sqd32(qx, qy, qz, __ldg(C.pts + s));
+      bool pass = inr && key_lt(d, (uint32_t)s, T.kd, T.kr);
+      uint32_t b = g.ballot(pass);
+      while (b) {
+        const int w = __ffs(b) - 1;
+        const float cd = g.shfl(d, w);
+        const uint32_t cr = g.shfl((uint32_t)s, w);
+        topk_insert(T, g, cd, cr, k);
+        pass = pass && ((int)g.lane > w) && key_lt(d, (uint32_t)s, T.kd, T.kr);
+        b = g.ballot(pass);
+      }
+      const uint32_t stop = g.ballot(valid && !inr);
+      if (COUNT) {
+        if (stop) {
+          const int t = __ffs(stop) - 1;
+          qc.entries += t + 1;
+          qc.coords += t;
+        } else {
+          const int nv = min(G, end - base);
+          qc.entries += nv;
+          qc.coords += nv;
+        }
+      }
+      if (stop) break;
+    }
+  }
+
+  // ---- output: sorted (d, rank), padded with (-1, +inf)
+#pragma unroll
+  for (int s = 0; s < S; ++s) {
+    const int p = s * G + (int)g.lane;
+    if (p < k) {
+      const uint32_t rr = T.r[s] & kRankMask;
+      const bool real = rr != kRankMask;
+      oi[p] = real ? (int32_t)rr : -1;
+      od[p] = real ? T.d[s] : INF;
+    }
+  }
+}
+
+// Writes a padded row (-1, +inf) for a query that cannot be served.
+template <int G>
+__device__ __forceinline__ void pad_row(const Grp<G>& g, int k, int32_t* oi, float* od) {
+  for (int p = (int)g.lane; p < k; p += G) {
+    oi[p] = -1;
+    od[p] = __int_as_float(0x7f800000);
+  }
+}
+
+}  // namespace mknn

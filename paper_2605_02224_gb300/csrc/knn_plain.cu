@@ -1,0 +1,127 @@
+// The plain query kernel: one cloud, a batch of queries, one group of G
+// lanes per query, grid-stride over the (optionally locality-sorted)
+// query order. Sized to the SM count times the resident blocks per SM.
+#include <mutex>
+
+#include "knn_device.cuh"
+#include "knn_kernels.h"
+
+namespace mknn {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+template <int G, int S, bool COUNT>
+__global__ void __launch_bounds__(kThreads) knn_plain_kernel(
+    CloudDev C, const float* __restrict__ q, int q_stride, int64_t nq, int k,
+    const int32_t* __restrict__ mq, int m_scalar, const int32_t* __restrict__ perm,
+    int32_t* __restrict__ out_idx, float* __restrict__ out_d2, int32_t* __restrict__ counters,
+    int32_t* __restrict__ err) {
+  const Grp<G> g;
+  const int64_t gid = ((int64_t)blockIdx.x * kThreads + threadIdx.x) / G;
+  const int64_t ngroups = ((int64_t)gridDim.x * kThreads) / G;
+  for (int64_t i = gid; i < nq; i += ngroups) {
+    const int64_t qi = perm ? (int64_t)__ldg(perm + i) : i;
+    const float* qp = q + qi * q_stride;
+    const float qx = __ldg(qp), qy = __ldg(qp + 1), qz = __ldg(qp + 2);
+    const int m = mq ? __ldg(mq + qi) : m_scalar;
+    int32_t* oi = out_idx + qi * k;
+    float* od = out_d2 + qi * k;
+    if (m < 1 || m > C.n) {
+      pad_row(g, k, oi, od);
+      if (g.lane == 0) atomicOr(err, 1);
+      continue;
+    }
+    QueryCounters qc{0, 0, 0, 0};
+    knn_query<G, S, COUNT>(C, g, qx, qy, qz, k, m, oi, od, qc);
+    if (COUNT && g.lane == 0) {
+      int32_t* c = counters + 4 * qi;
+      c[0] = qc.rows;
+      c[1] = qc.entries;
+      c[2] = qc.coords;
+      c[3] = qc.trans;
+    }
+  }
+}
+
+template <int G, int S, bool COUNT>
+cudaError_t run(const CloudDevHost& c, const PlainLaunch& L, cudaStream_t stream) {
+  static int occ = -1;
+  static std::mutex mu;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    if (occ < 0) {
+      cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+          &occ, knn_plain_kernel<G, S, COUNT>, kThreads, 0);
+      if (e != cudaSuccess) return e;
+      if (occ < 1) occ = 1;
+    }
+  }
+  const int per_sm = L.blocks_per_sm > 0 ? std::min(L.blocks_per_sm, occ) : occ;
+  const int64_t need = (L.nq * G + kThreads - 1) / kThreads;
+  int64_t blocks = (int64_t)num_sms() * per_sm;
+  if (need < blocks) blocks = need;
+  if (blocks < 1) blocks = 1;
+  CloudDev C{(const float4*)c.pts, c.rowp, c.succ, c.n};
+  knn_plain_kernel<G, S, COUNT><<<(unsigned)blocks, kThreads, 0, stream>>>(
+      C, L.q, L.q_stride, L.nq, L.k, L.m, L.m_scalar, L.perm, L.out_idx, L.out_d2, L.counters,
+      L.err);
+  return cudaGetLastError();
+}
+
+template <int G, bool COUNT>
+cudaError_t pick_s(const CloudDevHost& c, const PlainLaunch& L, cudaStream_t stream) {
+  const int need = (L.k + G - 1) / G;
+  if (need <= 1) return run<G, 1, COUNT>(c, L, stream);
+  if (need <= 2) return run<G, 2, COUNT>(c, L, stream);
+  if constexpr (G <= 16) {
+    if (need <= 4) return run<G, 4, COUNT>(c, L, stream);
+  }
+  if constexpr (G <= 8) {
+    if (need <= 8) return run<G, 8, COUNT>(c, L, stream);
+  }
+  if constexpr (G <= 4) {
+    if (need <= 16) return run<G, 16, COUNT>(c, L, stream);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <bool COUNT>
+cudaError_t pick_g(const CloudDevHost& c, const PlainLaunch& L, cudaStream_t stream) {
+  switch (L.lanes) {
+    case 4: return pick_s<4, COUNT>(c, L, stream);
+    case 8: return pick_s<8, COUNT>(c, L, stream);
+    case 16: return pick_s<16, COUNT>(c, L, stream);
+    case 32: return pick_s<32, COUNT>(c, L, stream);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace
+
+int num_sms() {
+  static int sms = -1;
+  static std::mutex mu;
+  std::lock_guard<std::mutex> lk(mu);
+  if (sms < 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+      sms = 1;
+  }
+  return sms;
+}
+
+int default_lanes(int k) {
+  (void)k;
+  return 8;
+}
+
+cudaError_t launch_knn_plain(const CloudDevHost& c, const PlainLaunch& L, cudaStream_t stream) {
+  if (L.nq == 0) return cudaSuccess;
+  if (L.counters) return pick_g<true>(c, L, stream);
+  return pick_g<false>(c, L, stream);
+}
+
+}  // namespace mknn

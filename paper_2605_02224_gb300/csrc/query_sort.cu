@@ -1,0 +1,116 @@
+// Query locality sort (counting sort by cell in a 64^3 grid, cells in
+// Morton order). Queries that land in the same or neighbouring cells are
+// then processed by neighbouring lanes, warps and blocks, so the successor
+// rows and coordinates they share are found in L1 and L2. The sort only
+// changes the processing order: each query's result goes to its own row.
+#include "knn_kernels.h"
+
+namespace mknn {
+
+namespace {
+
+__device__ __forceinline__ uint32_t spread3(uint32_t v) {  // 6 bits -> every third bit
+  uint32_t x = v & 0x3fu;
+  x = (x | (x << 8)) & 0x0000f00fu;
+  x = (x | (x << 4)) & 0x000c30c3u;
+  x = (x | (x << 2)) & 0x00249249u;
+  return x;
+}
+
+__global__ void qsort_hist(const float* __restrict__ q, int stride, int64_t nq, float lox,
+                           float loy, float loz, float sx, float sy, float sz,
+                           int32_t* __restrict__ cell, int32_t* __restrict__ hist) {
+  const int64_t step = (int64_t)gridDim.x * blockDim.x;
+  const float cmax = (float)((1 << kSortBits) - 1);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nq; i += step) {
+    const float* p = q + i * stride;
+    const float fx = fminf(fmaxf((__ldg(p) - lox) * sx, 0.f), cmax);
+    const float fy = fminf(fmaxf((__ldg(p + 1) - loy) * sy, 0.f), cmax);
+    const float fz = fminf(fmaxf((__ldg(p + 2) - loz) * sz, 0.f), cmax);
+    // a NaN coordinate maps to cell 0 (fminf/fmaxf drop NaN operands)
+    const uint32_t c = spread3((uint32_t)fx) | (spread3((uint32_t)fy) << 1) |
+                       (spread3((uint32_t)fz) << 2);
+    cell[i] = (int32_t)c;
+    atomicAdd(hist + c, 1);
+  }
+}
+
+// Exclusive scan of kSortCells counts in place, one block of 1024 threads.
+__global__ void __launch_bounds__(1024) qsort_scan(int32_t* __restrict__ hist) {
+  constexpr int kPer = kSortCells / 1024;
+  __shared__ int32_t warp_sums[32];
+  const int t = threadIdx.x;
+  int32_t local[kPer];
+  int32_t sum = 0;
+  for (int j = 0; j < kPer; ++j) {
+    local[j] = hist[t * kPer + j];
+    sum += local[j];
+  }
+  // inclusive scan of per-thread sums across the block
+  int32_t v = sum;
+  const int lane = t & 31, warp = t >> 5;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int32_t u = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += u;
+  }
+  if (lane == 31) warp_sums[warp] = v;
+  __syncthreads();
+  if (warp == 0) {
+    int32_t w = warp_sums[lane];
+    for (int o = 1; o < 32; o <<= 1) {
+      const int32_t u = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += u;
+    }
+    warp_sums[lane] = w;
+  }
+  __syncthreads();
+  int32_t run = v - sum + (warp > 0 ? warp_sums[warp - 1] : 0);
+  for (int j = 0; j < kPer; ++j) {
+    hist[t * kPer + j] = run;
+    run += local[j];
+  }
+}
+
+__global__ void qsort_scatter(const int32_t* __restrict__ cell, int64_t nq,
+                              int32_t* __restrict__ offs, int32_t* __restrict__ perm) {
+  const int64_t step = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nq; i += step) {
+    const int32_t pos = atomicAdd(offs + cell[i], 1);
+    perm[pos] = (int32_t)i;
+  }
+}
+
+inline size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+}  // namespace
+
+size_t sort_workspace_bytes(int64_t nq) {
+  return align256((size_t)kSortCells * 4) + align256((size_t)nq * 4);
+}
+
+cudaError_t launch_query_sort(const CloudDevHost& c, const float* q, int32_t q_stride, int64_t nq,
+                              void* workspace, int32_t* perm, cudaStream_t stream) {
+  char* w = (char*)workspace;
+  int32_t* hist = (int32_t*)w;
+  int32_t* cell = (int32_t*)(w + align256((size_t)kSortCells * 4));
+  if (nq == 0) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(hist, 0, (size_t)kSortCells * 4, stream);
+  if (e != cudaSuccess) return e;
+  const float cells = (float)(1 << kSortBits);
+  float s[3];
+  for (int i = 0; i < 3; ++i) {
+    const float ext = c.hi[i] - c.lo[i];
+    s[i] = ext > 0.f ? cells / ext : 0.f;
+  }
+  const int threads = 256;
+  int64_t blocks = (nq + threads - 1) / threads;
+  const int64_t cap = (int64_t)num_sms() * 8;
+  if (blocks > cap) blocks = cap;
+  qsort_hist<<<(unsigned)blocks, threads, 0, stream>>>(q, q_stride, nq, c.lo[0], c.lo[1], c.lo[2],
+                                                       s[0], s[1], s[2], cell, hist);
+  qsort_scan<<<1, 1024, 0, stream>>>(hist);
+  qsort_scatter<<<(unsigned)blocks, threads, 0, stream>>>(cell, nq, hist, perm);
+  return cudaGetLastError();
+}
+
+}  // namespace mknn

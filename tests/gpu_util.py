@@ -1,0 +1,44 @@
+"""Helpers for the GPU tests: cached builds and device launches through the C ABI."""
+from __future__ import annotations
+
+import hashlib
+import os
+import tempfile
+
+import numpy as np
+
+from paper_2605_02224_gb300 import Cloud
+from paper_2605_02224_gb300 import mknn as M
+
+_CACHE_DIR = os.path.join(tempfile.gettempdir(), "mknn_test_clouds")
+
+
+def built_cloud(points: np.ndarray, order: np.ndarray, tag: str) -> Cloud:
+    """Builds (or loads a cached build of) a cloud; cached by content hash."""
+    os.makedirs(_CACHE_DIR, exist_ok=True)
+    h = hashlib.sha1()
+    h.update(np.ascontiguousarray(points).tobytes())
+    h.update(np.ascontiguousarray(order).tobytes())
+    path = os.path.join(_CACHE_DIR, f"{tag}-{h.hexdigest()[:16]}.mknn")
+    if os.path.exists(path):
+        try:
+            return Cloud.load(path)
+        except M.MknnError:
+            os.remove(path)
+    c = Cloud.build(points, order)
+    c.save(path)
+    return c
+
+
+def run_knn(cloud: Cloud, Q: np.ndarray, k: int, m=None, **opt):
+    """Queries on the device; returns host numpy (idx, d2)."""
+    import torch
+    q = torch.from_numpy(np.ascontiguousarray(Q, np.float32)).cuda()
+    mt = None
+    if m is not None and not isinstance(m, (int, np.integer)):
+        mt = torch.from_numpy(np.ascontiguousarray(m, np.int32)).cuda()
+    elif m is not None:
+        mt = int(m)
+    idx, d2 = cloud.knn(q, k, mt, **opt)
+    torch.cuda.synchronize()
+    return idx.cpu().numpy(), d2.cpu().numpy()

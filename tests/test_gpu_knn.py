@@ -1,0 +1,218 @@
+"""Parity of the CUDA query path (through the C ABI) with the oracle."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle.dpknn as dp
+import oracle.knn as ok
+import workloads as W
+from paper_2605_02224_gb300 import Cloud
+from paper_2605_02224_gb300 import mknn as M
+from tests import parity
+from tests.gpu_util import built_cloud, run_knn
+
+pytestmark = pytest.mark.gpu
+
+LANES = (4, 8, 16, 32)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.init()
+
+
+# ------------------------------------------------------------ tiny, exhaustive
+
+@pytest.mark.parametrize("n", [1, 2, 5, 17, 64, 150])
+@pytest.mark.parametrize("table", ["complete", "built"])
+def test_tiny_exhaustive(n, table):
+    P, _ = W.uniform_cube(n, 100 + n)
+    order = W.permutation(n, 200 + n)
+    Pr = P[order]
+    if table == "complete":
+        rowp, succ = dp.complete_table(n)
+        c = Cloud.from_table(Pr, rowp, succ).upload()
+    else:
+        c = Cloud.build(P, order).upload()
+    Q = W.box_queries(60, 7, [-1.5] * 3, [1.5] * 3)
+    Q = np.concatenate([Q, Pr[: min(n, 20)]])          # queries exactly on sites
+    ks = sorted({1, 2, min(n, 8), min(n + 1, 64), 33, 64})
+    for lanes in LANES:
+        for k in ks:
+            for m in sorted({1, max(1, n // 2), n}):
+                idx, d2 = run_knn(c, Q, k, m, lanes=lanes, sort=1 if k % 2 else -1)
+                parity.check_rows(Pr, Q, k, m, idx, d2)
+    c.close()
+
+
+def test_small_sphere_workload_all_queries():
+    """2,000 points on the unit sphere, 10,000 queries, k = 8: every row."""
+    wl = W.small_sphere()
+    c = Cloud.build(wl.points, wl.order).upload()
+    Pr = wl.ranked_points()
+    for lanes in LANES:
+        idx, d2 = run_knn(c, wl.queries, wl.k, lanes=lanes)
+        parity.check_rows(Pr, wl.queries, wl.k, 0, idx, d2)
+    idx0, d20 = run_knn(c, wl.queries, wl.k)
+    assert c.check() == 0
+    c.close()
+
+
+def test_sphere_centre_closed_form():
+    """Origin against the 2,000-point sphere: every squared distance is 1 up
+    to float32 normalisation; the 64 returned ranks are distinct."""
+    wl = W.small_sphere(nq=1)
+    c = Cloud.build(wl.points, wl.order).upload()
+    Q = np.zeros((4, 3), np.float32)
+    for lanes in LANES:
+        idx, d2 = run_knn(c, Q, 64, lanes=lanes)
+        assert np.all(np.abs(d2 - 1.0) <= 1e-6)
+        assert all(np.unique(r).size == 64 for r in idx)
+        assert np.all(idx >= 0) and np.all(idx < 2000)
+    c.close()
+
+
+def test_lattice_rings_closed_form():
+    """Integer lattice (all cubes cospherical): k equal to cumulative ring
+    sizes returns whole rings, exact squared distances, ranks ascending
+    inside each ring."""
+    from tests import oracle_pins as pins
+    L = 16
+    P_in, _ = W.lattice(L)
+    order = W.permutation(P_in.shape[0], 5)
+    c = Cloud.build(P_in, order).upload()
+    P, rank_of = pins.lattice_setup(L, 5)
+    r3 = pins.read_r3()
+    rng = np.random.default_rng(0)
+    centres = rng.integers(5, L - 5, size=(50, 3)).astype(np.float32)
+    for k in (1, 7, 19, 27, 33):
+        for lanes in LANES:
+            idx, d2 = run_knn(c, centres, k, lanes=lanes)
+            parity.check_rows(P, centres, k, 0, idx, d2)
+            cum = np.cumsum([r3[s] for s in range(13)])
+            smax = int(np.searchsorted(cum, k))
+            want = np.concatenate([np.full(r3[s], float(s)) for s in range(smax + 1)])
+            assert np.all(d2 == want[None, :])
+    c.close()
+
+
+def test_prefix_bound_per_query_and_padding():
+    P, _ = W.bumpy_sphere(20000, 31)
+    order = W.permutation(20000, 32)
+    c = built_cloud(P, order, "bumpy20k")
+    c.upload()
+    Pr = P[order]
+    nq = 3000
+    Q = np.concatenate([W.box_queries(nq // 2, 33, [-1.3] * 3, [1.3] * 3),
+                        W.near_surface_queries("bumpy", nq - nq // 2, 34)])
+    u = W.uniform(35, 1, nq)
+    m = np.floor(np.exp(u * np.log(20000))).astype(np.int32)
+    m = np.clip(m, 1, 20000)
+    m[:50] = np.arange(1, 51)                       # m < k: padded rows
+    for k in (1, 10, 64):
+        for lanes in LANES:
+            idx, d2 = run_knn(c, Q, k, m, lanes=lanes)
+            parity.check_row_properties(idx, d2, k, m.astype(np.int64), 20000)
+            parity.check_rows(Pr, Q, k, m, idx, d2, rows=range(0, nq, 7))
+    assert c.check() == 0
+    c.close()
+
+
+def test_invalid_per_query_m_sets_flag_and_pads():
+    import torch
+    wl = W.small_sphere(nq=64)
+    c = Cloud.build(wl.points, wl.order).upload()
+    m = np.full(64, 2000, np.int32)
+    m[5] = 0
+    m[9] = 2001
+    idx, d2 = run_knn(c, wl.queries, 8, m)
+    assert np.all(idx[5] == -1) and np.all(np.isinf(d2[5]))
+    assert np.all(idx[9] == -1)
+    assert c.check() & 1
+    assert c.check() == 0
+    parity.check_rows(wl.ranked_points(), wl.queries, 8, m, idx, d2,
+                      rows=[i for i in range(64) if i not in (5, 9)])
+    with pytest.raises(M.MknnError):
+        c.knn(torch.zeros((4, 3), device="cuda"), 65)
+    with pytest.raises(M.MknnError):
+        c.knn(torch.zeros((4, 3), device="cuda"), 8, 2001)
+    idx, d2 = c.knn(torch.zeros((0, 3), device="cuda"), 8)
+    assert idx.shape == (0, 8)
+    c.close()
+
+
+def test_duplicates_and_degenerate_clouds():
+    P, _ = W.lattice(8)
+    P = np.concatenate([P, P[:100]])                 # exact duplicates, later ranks
+    n = P.shape[0]
+    order = W.permutation(n, 77)
+    c = Cloud.build(P, order).upload()
+    Pr = P[order]
+    Q = np.concatenate([W.box_queries(500, 78, [-1] * 3, [8] * 3), Pr[:100]]).astype(np.float32)
+    for k in (1, 2, 9, 27, 64):
+        for lanes in (8, 32):
+            idx, d2 = run_knn(c, Q, k, lanes=lanes)
+            parity.check_rows(Pr, Q, k, 0, idx, d2)
+    c.close()
+
+
+def test_host_buffer_entry_point_matches_device():
+    wl = W.small_sphere()
+    c = Cloud.build(wl.points, wl.order).upload()
+    idx, d2 = run_knn(c, wl.queries, 8)
+    hi, hd = c.knn_host(wl.queries, 8)
+    assert np.array_equal(hi, idx) and np.array_equal(hd, d2)
+    m = np.full(wl.nq, 777, np.int32)
+    hi, hd = c.knn_host(wl.queries, 8, m)
+    idx, d2 = run_knn(c, wl.queries, 8, m)
+    assert np.array_equal(hi, idx) and np.array_equal(hd, d2)
+    c.close()
+
+
+def test_counters_match_algorithm_restatement():
+    """Per-query rows opened / entries read / coordinates read / transition
+    sites counted by the kernel equal those of the step-by-step Alg. 1 + 2
+    (float64) for all but near-tie queries."""
+    import torch
+    P, _ = W.torus(30000, 11)
+    order = W.permutation(30000, 12)
+    c = built_cloud(P, order, "torus30k")
+    c.upload()
+    Pr = P[order]
+    _, rowp, succ = c.table()
+    Q = W.box_queries(400, 13, [-1.5, -1.5, -0.5], [1.5, 1.5, 0.5])
+    for k, lanes in ((1, 8), (16, 8), (16, 32), (5, 4)):
+        cnt = torch.zeros((Q.shape[0], 4), dtype=torch.int32, device="cuda")
+        idx, d2 = run_knn(c, Q, k, lanes=lanes, counters=cnt)
+        cnt = cnt.cpu().numpy()
+        same = 0
+        for i in range(Q.shape[0]):
+            cc = dp.Counters()
+            dp.knn_dp(Pr, rowp, succ, Q[i], k, 0, cc)
+            trans = len(dp.descent(Pr, rowp, succ, Q[i], 30000))
+            if tuple(cnt[i]) == (cc.rows, cc.entries, cc.coords, trans):
+                same += 1
+        assert same >= 0.99 * Q.shape[0], (k, lanes, same)
+    c.close()
+
+
+@pytest.mark.slow
+def test_large_torus_full_size_sampled():
+    """The 1M-point torus with 4M queries, k = 16, launched as the benchmark
+    launches it: every row's properties, and a sample of rows against the
+    oracle one by one."""
+    wl = W.large_torus()
+    c = built_cloud(wl.points, wl.order, "torus1m")
+    c.upload()
+    idx, d2 = run_knn(c, wl.queries, wl.k)
+    parity.check_row_properties(idx, d2, wl.k, np.full(wl.nq, wl.n, np.int64), wl.n)
+    Pr = wl.ranked_points()
+    rows = np.linspace(0, wl.nq - 1, 400).astype(np.int64)
+    parity.check_rows(Pr, wl.queries, wl.k, 0, idx, d2, rows=rows)
+    hi, hd = c.knn_host(wl.queries[:300000], wl.k)
+    assert np.array_equal(hi, idx[:300000]) and np.array_equal(hd, d2[:300000])
+    c.close()
