@@ -47,6 +47,7 @@ def _args():
     ap.add_argument("--n", type=int, default=1_000_000)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-sort", action="store_true", help="process queries in input order")
     return ap.parse_args()
 
 
@@ -245,13 +246,18 @@ def main():
     sptr = stream.cuda_stream
     lanes = args.lanes or 0
 
+    order = None if args.no_sort else perm
+    sort_flag = -1 if args.no_sort else 0
+
     def step(ev=None):
         if ev:
             ev[0].record(stream)
-        M.mknn_query_order(cloud.handle, q, nq, 3, perm, ws, ws_bytes, sptr)
+        if order is not None:
+            M.mknn_query_order(cloud.handle, q, nq, 3, perm, ws, ws_bytes, sptr)
         if ev:
             ev[1].record(stream)
-        M.mknn_knn_ex(cloud.handle, q, nq, 3, k, None, 0, idx, d2, sptr, lanes=lanes, order=perm)
+        M.mknn_knn_ex(cloud.handle, q, nq, 3, k, None, 0, idx, d2, sptr, lanes=lanes, order=order,
+                      sort=sort_flag)
         if ev:
             ev[2].record(stream)
 
@@ -261,8 +267,8 @@ def main():
 
     # algorithmic bytes of one launch, from the kernel's own counters (untimed)
     cnt = torch.zeros((nq, 4), dtype=torch.int32, device=dev)
-    M.mknn_knn_ex(cloud.handle, q, nq, 3, k, None, 0, idx, d2, sptr, lanes=lanes, order=perm,
-                  counters=cnt)
+    M.mknn_knn_ex(cloud.handle, q, nq, 3, k, None, 0, idx, d2, sptr, lanes=lanes, order=order,
+                  sort=sort_flag, counters=cnt)
     torch.cuda.synchronize()
     tot = cnt.to(torch.int64).sum(dim=0).cpu().numpy()
     rows, entries, coords, trans = (int(x) for x in tot)
@@ -335,7 +341,8 @@ def main():
                 "workload": f"torus R=1 r=0.3 sigma=1e-4, n={wl.n}, {nq} queries uniform in the "
                             f"bbox padded by 0.2, k={k}, m=n",
                 "n": wl.n, "nq": nq, "k": k, "E": st["entries"],
-                "lanes": lanes or 8, "query_order": "64^3 Morton cell counting sort",
+                "lanes": lanes or 8,
+                "query_order": "input order" if args.no_sort else "64^3 Morton cell counting sort",
                 "l2": "flushed before every timed step (256 MB write, outside the events)",
                 "build_seconds": build_s if build_s is not None else "cached",
                 "parallelism": f"replicas x{world}",
@@ -353,7 +360,7 @@ def main():
             "e2e": {"value": world * nq / e2e_s, "unit": UNIT,
                     "h2d_bytes_per_step": nq * 12, "d2h_bytes_per_step": nq * k * 8,
                     "ms_per_step": e2e_s * 1e3, "matches_device_path": agree},
-            "gpu_launches": 4 * args.steps,
+            "gpu_launches": (1 if args.no_sort else 4) * args.steps,
             "clocks": clk,
             "step_ms": step_ms,
         }
