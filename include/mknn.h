@@ -203,6 +203,29 @@ mknn_status mknn_knn_host(const mknn_cloud* cloud, const float* q, int64_t nq, i
                           int32_t k, const int32_t* m, int32_t m_scalar, int32_t* out_idx,
                           float* out_d2, mknn_stream_t stream);
 
+/* mknn_knn_noalloc: mknn_knn (with the locality sort) that allocates no
+ * memory at all during the call. The paper has no counterpart; this is an
+ * interface for callers that cannot allocate device memory while serving
+ * queries, e.g. a process whose memory pool already holds all the device
+ * memory it may use (so an allocation would fail), or a latency-bound
+ * loop that cannot afford the synchronisation cudaMalloc/cudaFree can
+ * cause. Its scratch is a fixed device array inside the library
+ * (9 MiB + 512 B) that every GPU using this entry point holds until the
+ * process exits.
+ *   Arguments, layout, results and errors are those of mknn_knn, except:
+ *   nq must be at most mknn_knn_noalloc_max_queries() (2^20); larger nq
+ *   returns EINVAL with a message naming the limit (split the batch).
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture. All calls share the one array: calls whose
+ * work overlaps on the GPU (other streams or host threads) race on it and
+ * must be serialised by the caller. Nothing carries over between calls:
+ * the parts that must start at zero are cleared by each call. */
+mknn_status mknn_knn_noalloc(const mknn_cloud* cloud, const float* q, int64_t nq, int32_t q_stride,
+                             int32_t k, const int32_t* m, int32_t m_scalar, int32_t* out_idx,
+                             float* out_d2, mknn_stream_t stream);
+int64_t mknn_knn_noalloc_max_queries(void);
+
 /* Reads and clears the cloud's device error flags (synchronises the
  * device). Bit 0: a per-query m was outside [1, n]. */
 mknn_status mknn_cloud_check(const mknn_cloud* cloud, int32_t* flags);

@@ -89,6 +89,8 @@ def _declare(L):
         "mknn_query_order_workspace_size": (sz, [i64]),
         "mknn_query_order": (i32, [vp, vp, i64, i32, vp, vp, sz, vp]),
         "mknn_cloud_validate": (i32, [vp, vp, vp]),
+        "mknn_knn_noalloc": (i32, [vp, vp, i64, i32, i32, vp, i32, vp, vp, vp]),
+        "mknn_knn_noalloc_max_queries": (i64, []),
         "mknn_orient3d": (i32, [vp, vp, vp, vp]),
         "mknn_insphere": (i32, [vp, vp, vp, vp, vp]),
         "mknn_orient3d_exact": (i32, [vp, vp, vp, vp]),
@@ -255,6 +257,20 @@ def mknn_knn_host(cloud: int, q, k: int, m=None, m_scalar: int = 0, out_idx=None
     _check(lib().mknn_knn_host(cloud, _ptr(q), nq, stride, k, _ptr(m), m_scalar, _ptr(out_idx),
                                _ptr(out_d2), stream or None))
     return out_idx, out_d2
+
+
+def mknn_knn_noalloc(cloud: int, q, nq: int, q_stride: int, k: int, m, m_scalar: int, out_idx,
+                     out_d2, stream: int = 0):
+    """mknn_knn for callers that cannot allocate device memory during a
+    call: its scratch is a fixed array inside the library (up to
+    mknn_knn_noalloc_max_queries() queries per call; concurrent calls on
+    one device must be serialised)."""
+    _check(lib().mknn_knn_noalloc(cloud, _ptr(q), nq, q_stride, k, _ptr(m), m_scalar,
+                                  _ptr(out_idx), _ptr(out_d2), stream or None))
+
+
+def mknn_knn_noalloc_max_queries() -> int:
+    return int(lib().mknn_knn_noalloc_max_queries())
 
 
 def mknn_cloud_check(cloud: int) -> int:
