@@ -44,10 +44,16 @@ def _args():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--lanes", type=int, default=0)
     ap.add_argument("--nq", type=int, default=4_000_000)
+    ap.add_argument("--k", type=int, default=16)
+    ap.add_argument("--placement", type=int, default=0,
+                    help="one-lane candidate lists: 0 default, 1 registers, 2 shared-memory tile")
     ap.add_argument("--n", type=int, default=1_000_000)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-sort", action="store_true", help="process queries in input order")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving section")
+    ap.add_argument("--serve-requests", type=int, default=400)
+    ap.add_argument("--workload", default="torus", choices=["torus", "batch", "prefix"])
     return ap.parse_args()
 
 
@@ -148,10 +154,11 @@ class Clocks:
 
 def _cloud_cache(points, order, tag):
     from paper_2605_02224_gb300 import Cloud
-    d = os.path.join("/tmp", "mknn_bench_clouds")
+    d = os.path.join("/tmp", "mknn_clouds")
     os.makedirs(d, exist_ok=True)
-    h = hashlib.sha1(points.tobytes() + order.tobytes()).hexdigest()[:16]
-    path = os.path.join(d, f"{tag}-{h}.mknn")
+    h = hashlib.sha1(np.ascontiguousarray(points).tobytes() +
+                     np.ascontiguousarray(order).tobytes()).hexdigest()[:16]
+    path = os.path.join(d, f"{h}.mknn")
     if os.path.exists(path):
         try:
             return Cloud.load(path), None
@@ -185,7 +192,7 @@ def run_reference(args, rank, world):
     if rank != 0:
         return
     import workloads as W
-    wl = W.large_torus(n=args.n, nq=args.nq)
+    wl = W.large_torus(n=args.n, nq=args.nq, k=args.k)
     P = wl.ranked_points()
     per_step = max(8, int(args.cpu_seconds * 2))   # ~0.5 s per query budgeted below
     rates = []
@@ -213,6 +220,195 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def _build_many(wls, tag):
+    """Builds (or loads cached builds of) several clouds in parallel host threads."""
+    from concurrent.futures import ThreadPoolExecutor
+    with ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 4)) as ex:
+        res = list(ex.map(lambda w: _cloud_cache(w.points, w.order, f"{tag}-{w.n}"), wls))
+    built = [r[1] for r in res if r[1] is not None]
+    return [r[0] for r in res], (max(built) if built else None)
+
+
+def serving_section(args, M, torch):
+    """Serving workload: 16 resident clouds (100k-4M sites, mixed surfaces),
+    Poisson arrivals at 0.5 / 0.8 / 0.95 of the plain path's saturation rate;
+    each request 1..65536 queries, k in 1..64, m in [n/10, n]. The batched
+    server (continuous batching, persistent kernel) against the baseline
+    that runs each request alone with the plain kernel, in arrival order, on
+    one stream. Same request sequence for every run (arrival times scaled)."""
+    import workloads as W
+    wls = W.serve_clouds()
+    clouds, build_s = _build_many(wls, "serve")
+    for c in clouds:
+        c.upload()
+    n_req = args.serve_requests
+    reqs = W.serve_requests(wls, n_req, 1.0, seed=42)
+    bufs = []
+    for r in reqs:
+        q = torch.from_numpy(r.queries).pin_memory()
+        bufs.append((q, torch.empty((r.queries.shape[0], r.k), dtype=torch.int32).pin_memory(),
+                     torch.empty((r.queries.shape[0], r.k), dtype=torch.float32).pin_memory()))
+    total_q = int(sum(r.queries.shape[0] for r in reqs))
+
+    def run(plain: int, rate):
+        srv = M.mknn_server_create(slots=1 if plain else 3, plain=plain, mem_budget=4 << 30)
+        ids = [M.mknn_server_add_cloud(srv, c.handle) for c in clouds]
+        for r, (q, oi, od) in list(zip(reqs, bufs))[:8]:            # warm-up
+            M.mknn_server_submit(srv, ids[r.cloud], q, r.k, r.m, oi, od)
+        M.mknn_server_drain(srv, 300.0)
+        M.mknn_server_reset_stats(srv)
+        t0 = time.perf_counter()
+        for r, (q, oi, od) in zip(reqs, bufs):
+            if rate is not None:
+                delay = r.arrival_s / rate - (time.perf_counter() - t0)
+                if delay > 0:
+                    time.sleep(delay)
+            M.mknn_server_submit(srv, ids[r.cloud], q, r.k, r.m, oi, od)
+        M.mknn_server_drain(srv, 600.0)
+        st = M.mknn_server_stats(srv)
+        M.mknn_server_destroy(srv, 60.0)
+        return {"qps": st["qps"], "rps": st["completed"] / max(st["elapsed_s"], 1e-9),
+                "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"],
+                "launches": st["launches"],
+                "requests_per_launch": st["mean_requests_per_launch"]}
+
+    sat_plain = run(1, None)
+    sat_batched = run(0, None)
+    loads = []
+    for f in (0.5, 0.8, 0.95):
+        rate = f * sat_plain["rps"]
+        loads.append({"offered": f, "rate_rps": rate, "batched": run(0, rate),
+                      "plain": run(1, rate)})
+    return {
+        "workload": f"16 resident clouds ({sum(w.n for w in wls)} sites, 100k-4M, mixed "
+                    f"surfaces); {n_req} requests, {total_q} queries, Poisson arrivals",
+        "build_seconds_max": build_s if build_s is not None else "cached",
+        "saturation": {"plain": sat_plain, "batched": sat_batched},
+        "loads": loads,
+    }
+
+
+def batch_workload(args, M, torch):
+    """Batching workload: 64 clouds (log-uniform 10k-2M sites, mixed
+    surfaces), 2n queries per cloud, k from {1,4,8,16,32}; one persistent
+    launch per step (graph replay, autotuned) against one plain launch per
+    cloud in sequence on one stream."""
+    import workloads as W
+    wls = W.batch_clouds()
+    clouds, build_s = _build_many(wls, "batch")
+    dev = torch.device("cuda", torch.cuda.current_device())
+    reqs = []
+    for wl, c in zip(wls, clouds):
+        c.upload()
+        q = torch.from_numpy(wl.queries).to(dev)
+        reqs.append(dict(cloud=c.handle, q=q, nq=wl.nq, q_stride=3, k=wl.k, m=None, m_scalar=0,
+                         out_idx=torch.empty((wl.nq, wl.k), dtype=torch.int32, device=dev),
+                         out_d2=torch.empty((wl.nq, wl.k), dtype=torch.float32, device=dev)))
+    stream = torch.cuda.current_stream(dev)
+    s = stream.cuda_stream
+    t0 = time.perf_counter()
+    M.mknn_batch_tune(reqs, 1 << 16, s)
+    tune_s = time.perf_counter() - t0
+    plan = M.mknn_batch_create(reqs)
+    lanes, items, grid = M.mknn_batch_info(plan, len(reqs))
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    nq = int(sum(r["nq"] for r in reqs))
+
+    def timed(fn):
+        for _ in range(max(3, args.warmup)):
+            fn()
+        torch.cuda.synchronize()
+        ms = []
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        return float(np.mean(ms))
+
+    ms_batch = timed(lambda: M.mknn_batch_run(plan, s))
+    ref = [r["out_idx"].clone() for r in reqs]
+
+    def plain():
+        for r in reqs:
+            M.mknn_knn(r["cloud"], r["q"], r["nq"], 3, r["k"], None, 0, r["out_idx"],
+                       r["out_d2"], s)
+
+    ms_plain = timed(plain)
+    same = all(torch.equal(a, r["out_idx"]) for a, r in zip(ref, reqs))
+    M.mknn_batch_free(plan)
+    line = {
+        "metric": "batched k-NN queries/sec (64 clouds, one persistent launch, autotuned)",
+        "value": nq / (ms_batch / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_batch, "higher_is_better": True,
+        "data": "synthetic", "dtype": "f32",
+        "config": {"workload": f"64 clouds, {sum(w.n for w in wls)} sites, {nq} queries "
+                               f"(half box, half near-surface), k in {{1,4,8,16,32}}",
+                   "l2": "flushed before every timed step", "items": items, "grid": grid,
+                   "lanes_chosen": {str(l): int((lanes == l).sum()) for l in set(lanes.tolist())},
+                   "tune_seconds": tune_s,
+                   "build_seconds_max": build_s if build_s is not None else "cached"},
+        "plain_one_launch_per_cloud": {"value": nq / (ms_plain / 1e3), "ms_per_step": ms_plain},
+        "results_identical": same,
+        "gpu_launches": (1 + 4 * len(reqs)) * args.steps,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def prefix_workload(args, M, torch):
+    """Prefix workload: 4M-site bumpy sphere, 8M queries (half volume, half
+    near-surface), per-query m log-uniform in [1000, n], k = 10."""
+    import workloads as W
+    wl = W.prefix_bumpy()
+    cloud, build_s = _cloud_cache(wl.points, wl.order, f"bumpy{wl.n}")
+    cloud.upload()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    q = torch.from_numpy(wl.queries).to(dev)
+    m = torch.from_numpy(wl.m).to(dev)
+    nq, k = wl.nq, wl.k
+    idx = torch.empty((nq, k), dtype=torch.int32, device=dev)
+    d2 = torch.empty((nq, k), dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    s = stream.cuda_stream
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    lanes = args.lanes or 0
+    for _ in range(max(3, args.warmup)):
+        M.mknn_knn_ex(cloud.handle, q, nq, 3, k, m, 0, idx, d2, s, lanes=lanes)
+    cnt = torch.zeros((nq, 4), dtype=torch.int32, device=dev)
+    M.mknn_knn_ex(cloud.handle, q, nq, 3, k, m, 0, idx, d2, s, lanes=lanes, counters=cnt)
+    torch.cuda.synchronize()
+    rows, entries, coords, trans = (int(x) for x in cnt.to(torch.int64).sum(dim=0).cpu().numpy())
+    alg = 12 * nq + 4 * nq + 8 * rows + 4 * entries + 12 * coords + 8 * k * nq
+    ms = []
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        M.mknn_knn_ex(cloud.handle, q, nq, 3, k, m, 0, idx, d2, s, lanes=lanes)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    t = float(np.mean(ms))
+    peak, kind = _peaks()
+    line = {
+        "metric": "prefix k-NN queries/sec (k=10, 4M-pt bumpy sphere, per-query m)",
+        "value": nq / (t / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t, "higher_is_better": True, "data": "synthetic",
+        "dtype": "f32",
+        "config": {"workload": f"bumpy sphere n={wl.n}, {nq} queries, m log-uniform in "
+                               f"[1000, n], k={k}", "E": cloud.stats()["entries"],
+                   "build_seconds": build_s if build_s is not None else "cached",
+                   "l2": "flushed before every timed step"},
+        "roofline": {"bound": "hbm", "achieved": alg / (t / 1e3) / 1e9, "peak": peak,
+                     "unit": "GB/s", "frac": alg / (t / 1e3) / 1e9 / peak,
+                     "alg_bytes_per_query": alg / nq, "peak_source": kind},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = _args()
     rank, world, local = _dist_env()
@@ -224,12 +420,18 @@ def main():
     from paper_2605_02224_gb300 import mknn as M
 
     torch.cuda.set_device(local)
+    if args.workload == "batch":
+        batch_workload(args, M, torch)
+        return
+    if args.workload == "prefix":
+        prefix_workload(args, M, torch)
+        return
     dist = None
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
-    wl = W.large_torus(n=args.n, nq=args.nq)
+    wl = W.large_torus(n=args.n, nq=args.nq, k=args.k)
     cloud, build_s = _cloud_cache(wl.points, wl.order, f"torus{wl.n}")
     cloud.upload()
     st = cloud.stats()
@@ -257,7 +459,7 @@ def main():
         if ev:
             ev[1].record(stream)
         M.mknn_knn_ex(cloud.handle, q, nq, 3, k, None, 0, idx, d2, sptr, lanes=lanes, order=order,
-                      sort=sort_flag)
+                      sort=sort_flag, placement=args.placement)
         if ev:
             ev[2].record(stream)
 
@@ -324,6 +526,10 @@ def main():
     khash = _kernel_hash()
     traffic = _profiled_traffic(khash, wl.n, nq)
 
+    serving = None
+    if rank == 0 and world == 1 and not args.no_serve:
+        serving = serving_section(args, M, torch)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, s, dt = _oracle_rate(wl.ranked_points(), wl.queries, k, args.cpu_seconds)
@@ -360,9 +566,10 @@ def main():
             "e2e": {"value": world * nq / e2e_s, "unit": UNIT,
                     "h2d_bytes_per_step": nq * 12, "d2h_bytes_per_step": nq * k * 8,
                     "ms_per_step": e2e_s * 1e3, "matches_device_path": agree},
-            "gpu_launches": (1 if args.no_sort else 4) * args.steps,
+            "gpu_launches": (1 if args.no_sort else 5) * args.steps,
             "clocks": clk,
             "step_ms": step_ms,
+            "serving": serving,
         }
         print(json.dumps(line), flush=True)
     if dist:

@@ -167,7 +167,11 @@ typedef struct {
   size_t workspace_bytes;
   const int32_t* order; /* device int32[nq] processing order (e.g. from
                            mknn_query_order) or NULL; overrides sort */
-  int32_t reserved[4];
+  int32_t placement;    /* candidate list of a one-lane query: 0 = default,
+                           1 = registers (each thread walks alone),
+                           2 = shared memory (a warp walks 32 queries'
+                           rows together) */
+  int32_t reserved[3];
 } mknn_knn_opts;
 
 /* Locality order of a query batch, the one mknn_knn_ex applies when sort
@@ -210,7 +214,7 @@ mknn_status mknn_knn_host(const mknn_cloud* cloud, const float* q, int64_t nq, i
  * memory it may use (so an allocation would fail), or a latency-bound
  * loop that cannot afford the synchronisation cudaMalloc/cudaFree can
  * cause. Its scratch is a fixed device array inside the library
- * (9 MiB + 512 B) that every GPU using this entry point holds until the
+ * (9 MiB + 1.5 KiB) that every GPU using this entry point holds until the
  * process exits.
  *   Arguments, layout, results and errors are those of mknn_knn, except:
  *   nq must be at most mknn_knn_noalloc_max_queries() (2^20); larger nq
@@ -229,6 +233,134 @@ int64_t mknn_knn_noalloc_max_queries(void);
 /* Reads and clears the cloud's device error flags (synchronises the
  * device). Bit 0: a per-query m was outside [1, n]. */
 mknn_status mknn_cloud_check(const mknn_cloud* cloud, int32_t* flags);
+
+/* ------------------------------------------------------- batched queries
+ * Many requests, each on its own cloud with its own k and m, answered by
+ * one persistent kernel launch that drains a device work queue (items of a
+ * few rounds of one request's queries). Per request the kernel variant
+ * (lanes per query, candidate slots) comes from the tuning table, filled by
+ * mknn_batch_tune, or a default. A plan captures its launches (query
+ * locality sorts + the persistent kernel) in a CUDA graph and replays it.
+ * The paper answers queries one at a time on a CPU (Sec. 5.1); batching
+ * many clouds into one launch is this library's GPU form of the same
+ * per-query Algorithms 1-2, with identical results. */
+typedef struct {
+  const mknn_cloud* cloud; /* uploaded on the current device */
+  const float* q;          /* device float32, nq rows of q_stride floats */
+  int64_t nq;
+  int32_t q_stride;        /* >= 3 */
+  int32_t k;               /* 1..MKNN_MAX_K */
+  const int32_t* m;        /* device int32[nq] or NULL */
+  int32_t m_scalar;        /* when m is NULL: 0 = n, else 1..n */
+  int32_t* out_idx;        /* device int32[nq*k] */
+  float* out_d2;           /* device float32[nq*k] */
+} mknn_batch_req;
+
+typedef struct {
+  int32_t lanes;          /* 0 = tuned per request, else 4, 8, 16 or 32 for all */
+  int32_t sort;           /* 0 = sort requests with >= 4096 queries, 1 = all, -1 = none */
+  int32_t item_rounds;    /* rounds of the group width per work item (0 = 8) */
+  int32_t blocks_per_sm;  /* 0 = occupancy limit */
+  int32_t graph;          /* 0 = capture a CUDA graph (default), -1 = plain launches */
+  int32_t reserved[7];
+} mknn_batch_opts;
+
+typedef struct mknn_batch mknn_batch;
+
+/* Makes a plan: validates the requests, picks each request's variant,
+ * cuts the work items, allocates the plan's device memory (queue, request
+ * table, sort scratch) and captures the graph. The request pointers are
+ * baked into the plan: the buffers must stay valid while the plan is used;
+ * their contents may change between runs. Errors: EINVAL, ENOMEM, ECUDA. */
+mknn_status mknn_batch_create(const mknn_batch_req* reqs, int32_t nreq,
+                              const mknn_batch_opts* opts, mknn_batch** out);
+/* Enqueues one run of the plan on the stream (asynchronous). Runs of one
+ * plan must not overlap on the device (they share the queue counter). */
+mknn_status mknn_batch_run(mknn_batch* plan, mknn_stream_t stream);
+/* Lanes chosen per request (int32[nreq], may be NULL), work items, grid. */
+mknn_status mknn_batch_info(const mknn_batch* plan, int32_t* lanes, int64_t* items, int32_t* grid);
+mknn_status mknn_batch_free(mknn_batch* plan);
+/* One-shot: create (without a graph), run, synchronise the stream, free. */
+mknn_status mknn_knn_batch(const mknn_batch_req* reqs, int32_t nreq, const mknn_batch_opts* opts,
+                           mknn_stream_t stream);
+
+/* Autotuner: for every distinct (k, floor(log2 n)) among the requests,
+ * times each kernel variant - one query per thread with a shared-memory
+ * candidate list (lanes 1), or a group of 4, 8, 16 or 32 lanes with the
+ * list in registers - on max(sample, 2 x SMs x 2048) queries of that
+ * request (tiled when it has fewer; plain launches, best of 2 after a
+ * warm-up) and records the fastest in the process-wide tuning table. Plans,
+ * plain launches and the server take the table's entry, widened to more
+ * lanes when a launch is too small to fill the GPU one query per thread.
+ * Synchronises the stream. Errors: EINVAL, ENOMEM, ECUDA. */
+mknn_status mknn_batch_tune(const mknn_batch_req* reqs, int32_t nreq, int64_t sample,
+                            mknn_stream_t stream);
+/* Tuning table as text ("k log2n lanes" per line). */
+mknn_status mknn_tune_save(const char* path);
+mknn_status mknn_tune_load(const char* path);
+
+/* ---------------------------------------------------------------- serving
+ * A request loop over resident clouds with continuous batching: a
+ * scheduler thread packs pending requests (any cloud, k and m) into the
+ * next launch of the persistent kernel as soon as a launch slot and
+ * device memory are free; several launches are in flight on separate
+ * streams, so requests that arrive while others run are admitted and
+ * their copies and kernels overlap on the device. Admission is by device
+ * memory: each request needs nq * (12 + 8 k) bytes of the staging budget
+ * while it is in flight. Latency = completion time - submit time. */
+typedef struct {
+  int32_t slots;            /* launches in flight (streams), 0 = 3 */
+  int32_t plain;            /* 1 = baseline mode: each request alone, in
+                               arrival order, with mknn_knn on one stream */
+  size_t mem_budget;        /* device staging bytes, 0 = 3 GiB */
+  int64_t max_batch_queries;/* queries packed into one launch, 0 = 2^17 (a larger
+                               request still runs, alone) */
+  int32_t lanes;            /* 0 = tuned/default per request */
+  int32_t reserved[7];
+} mknn_server_opts;
+
+typedef struct {
+  int32_t cloud;            /* id from mknn_server_add_cloud */
+  int32_t k;                /* 1..MKNN_MAX_K */
+  int32_t m;                /* prefix bound for every query: 0 = n, else 1..n */
+  int32_t reserved;
+  const float* q;           /* HOST float32[nq*3], valid until the request is done */
+  int64_t nq;               /* >= 1 */
+  int32_t* out_idx;         /* HOST int32[nq*k], written when done */
+  float* out_d2;            /* HOST float32[nq*k] */
+} mknn_request;
+
+typedef struct {
+  int64_t submitted, completed, failed, queries, launches;
+  double elapsed_s;         /* first submit to last completion */
+  double qps;               /* completed queries / elapsed_s */
+  double p50_ms, p99_ms, mean_ms, max_ms;
+  double mean_requests_per_launch;
+} mknn_serving_stats;
+
+typedef struct mknn_server mknn_server;
+
+/* Starts the scheduler thread on the current device. Errors: ENOMEM, ECUDA. */
+mknn_status mknn_server_create(const mknn_server_opts* opts, mknn_server** out);
+/* Makes a cloud resident (uploads it if needed) and holds it: freeing it
+ * returns EBUSY until the server is destroyed. *id receives its index. */
+mknn_status mknn_server_add_cloud(mknn_server* s, mknn_cloud* cloud, int32_t* id);
+/* Queues a request; *ticket identifies it. EINVAL for a bad request,
+ * ENOMEM if it alone exceeds the memory budget. Thread-safe. */
+mknn_status mknn_server_submit(mknn_server* s, const mknn_request* req, uint64_t* ticket);
+/* *state: 0 pending, 1 done, or minus a status code if it failed. */
+mknn_status mknn_server_poll(mknn_server* s, uint64_t ticket, int32_t* state);
+/* Waits (at most timeout_s seconds) until every submitted request is done;
+ * ETIMEOUT if the wait runs out. */
+mknn_status mknn_server_drain(mknn_server* s, double timeout_s);
+mknn_status mknn_server_stats(mknn_server* s, mknn_serving_stats* out);
+/* Completed requests' latencies in ms, in ticket order; *count = number
+ * written (at most cap). Resets nothing. */
+mknn_status mknn_server_latencies(mknn_server* s, double* ms, int64_t cap, int64_t* count);
+/* Clears the statistics and latency records (not the queue). */
+mknn_status mknn_server_reset_stats(mknn_server* s);
+/* Drains (up to timeout_s), stops the thread, releases the held clouds. */
+mknn_status mknn_server_destroy(mknn_server* s, double timeout_s);
 
 /* ------------------------------------------------------------ diagnostics
  * Exact geometric predicates used by the builder (float32 inputs):

@@ -1,0 +1,637 @@
+// Persistent multi-cloud query kernel, its work plan, the autotuner that
+// picks the per-request kernel variant, and the CUDA graph that replays a
+// plan.
+//
+// A plan covers many requests, each (cloud, queries, k, m, outputs). Every
+// request is cut into work items of a few rounds of its group width; one
+// persistent launch (SM count x resident blocks) drains the item queue:
+// each warp takes the next item with one atomic and serves it with the
+// variant (lanes per query G, candidate slots per lane S) the tuner chose
+// for that request's (k, cloud size). Items of one request are contiguous
+// in the queue, so the warps working at any moment share one cloud's table
+// in L2; requests are queued by decreasing estimated cost so that the
+// queue ends with short items.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/mknn.h"
+#include "batch.h"
+#include "cloud.h"
+#include "knn_device.cuh"
+#include "knn_kernels.h"
+
+namespace mknn {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+// Variants compiled into the persistent kernel: (G, S) with G*S <= 64.
+struct VariantDesc {
+  int g, s;
+};
+// G = 1 is one query per thread with its candidate list in shared memory
+// (any k <= 64); the others keep a group's list in registers.
+constexpr VariantDesc kVariants[] = {{4, 1},  {4, 2},  {4, 4},  {8, 1},  {8, 2},
+                                     {8, 4},  {8, 8},  {16, 1}, {16, 2}, {16, 4},
+                                     {32, 1}, {32, 2}, {1, 64}};
+constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
+constexpr int kSmemVariant = 12;
+
+}  // namespace
+
+int variant_index(int g, int k) {
+  int best = -1;
+  for (int i = 0; i < kNumVariants; ++i)
+    if (kVariants[i].g == g && kVariants[i].g * kVariants[i].s >= k && k >= 1) {
+      if (best < 0 || kVariants[i].s < kVariants[best].s) best = i;
+    }
+  return best;
+}
+
+namespace {
+
+// This thread's column of its warp's shared-memory candidate lists.
+__device__ __forceinline__ void smem_columns(int kcap, float** dcol, uint32_t** rcol) {
+  extern __shared__ uint32_t batch_lists[];
+  const int warp = (int)(threadIdx.x >> 5), lane = (int)(threadIdx.x & 31u);
+  uint32_t* wbase = batch_lists + (size_t)warp * 2 * kcap * 32;
+  *dcol = reinterpret_cast<float*>(wbase) + lane;
+  *rcol = wbase + kcap * 32 + lane;
+}
+
+__device__ __forceinline__ void serve_item_smem(const ReqDev& R, const Item& w, float* dcol,
+                                                uint32_t* rcol) {
+  const int lane = (int)(threadIdx.x & 31u);
+  const CloudDev C{R.pts, R.rowp, R.succ, R.n};
+  for (int i = w.begin + lane; i < w.end; i += 32) {
+    const int64_t qi = R.perm ? (int64_t)__ldg(R.perm + i) : (int64_t)i;
+    const float* qp = R.q + qi * R.q_stride;
+    const float qx = __ldg(qp), qy = __ldg(qp + 1), qz = __ldg(qp + 2);
+    const int m = R.m ? __ldg(R.m + qi) : R.m_scalar;
+    int32_t* oi = R.out_idx + qi * R.k;
+    float* od = R.out_d2 + qi * R.k;
+    if (m < 1 || m > C.n) {
+      for (int p = 0; p < R.k; ++p) {
+        oi[p] = -1;
+        od[p] = __int_as_float(0x7f800000);
+      }
+      atomicOr(R.err, 1);
+      continue;
+    }
+    knn_query_smem(C, qx, qy, qz, R.k, m, dcol, rcol, oi, od);
+  }
+}
+
+template <int G, int S>
+__device__ __forceinline__ void serve_item(const ReqDev& R, const Item& w) {
+  const Grp<G> g;
+  const int gi = (int)((threadIdx.x & 31u) / G);
+  constexpr int kGroups = 32 / G;
+  const CloudDev C{R.pts, R.rowp, R.succ, R.n};
+  for (int i = w.begin + gi; i < w.end; i += kGroups) {
+    const int64_t qi = R.perm ? (int64_t)__ldg(R.perm + i) : (int64_t)i;
+    const float* qp = R.q + qi * R.q_stride;
+    const float qx = __ldg(qp), qy = __ldg(qp + 1), qz = __ldg(qp + 2);
+    const int m = R.m ? __ldg(R.m + qi) : R.m_scalar;
+    int32_t* oi = R.out_idx + qi * R.k;
+    float* od = R.out_d2 + qi * R.k;
+    if (m < 1 || m > C.n) {
+      pad_row(g, R.k, oi, od);
+      if (g.lane == 0) atomicOr(R.err, 1);
+      continue;
+    }
+    QueryCounters qc{0, 0, 0, 0};
+    knn_query<G, S, false>(C, g, qx, qy, qz, R.k, m, oi, od, qc);
+  }
+}
+
+// All variants. Three resident blocks per SM caps the variants' union at
+// 80 registers (a few bytes of spill in the largest) instead of 118.
+__global__ void __launch_bounds__(kThreads, 3) knn_batch_kernel(const ReqDev* __restrict__ reqs,
+                                                             const Item* __restrict__ items,
+                                                             int nitems, int* __restrict__ next,
+                                                             int kcap) {
+  const uint32_t lane = threadIdx.x & 31u;
+  float* dcol = nullptr;
+  uint32_t* rcol = nullptr;
+  if (kcap > 0) smem_columns(kcap, &dcol, &rcol);
+  for (;;) {
+    int it = 0;
+    if (lane == 0) it = atomicAdd(next, 1);
+    it = __shfl_sync(0xffffffffu, it, 0);
+    if (it >= nitems) return;
+    const Item w = items[it];
+    const ReqDev R = reqs[w.req];
+    switch (w.variant) {
+      case 0: serve_item<4, 1>(R, w); break;
+      case 1: serve_item<4, 2>(R, w); break;
+      case 2: serve_item<4, 4>(R, w); break;
+      case 3: serve_item<8, 1>(R, w); break;
+      case 4: serve_item<8, 2>(R, w); break;
+      case 5: serve_item<8, 4>(R, w); break;
+      case 6: serve_item<8, 8>(R, w); break;
+      case 7: serve_item<16, 1>(R, w); break;
+      case 8: serve_item<16, 2>(R, w); break;
+      case 9: serve_item<16, 4>(R, w); break;
+      case 10: serve_item<32, 1>(R, w); break;
+      case 11: serve_item<32, 2>(R, w); break;
+      case kSmemVariant: serve_item_smem(R, w, dcol, rcol); break;
+      default: break;
+    }
+    __syncwarp();
+  }
+}
+
+// The shared-memory one-query-per-thread variant alone (48 registers):
+// used when every request of a launch takes it, the default.
+template <int THREADS>
+__global__ void __launch_bounds__(THREADS) knn_batch_smem_kernel(const ReqDev* __restrict__ reqs,
+                                                                 const Item* __restrict__ items,
+                                                                 int nitems,
+                                                                 int* __restrict__ next,
+                                                                 int kcap) {
+  const uint32_t lane = threadIdx.x & 31u;
+  float* dcol;
+  uint32_t* rcol;
+  smem_columns(kcap, &dcol, &rcol);
+  for (;;) {
+    int it = 0;
+    if (lane == 0) it = atomicAdd(next, 1);
+    it = __shfl_sync(0xffffffffu, it, 0);
+    if (it >= nitems) return;
+    const Item w = items[it];
+    serve_item_smem(reqs[w.req], w, dcol, rcol);
+    __syncwarp();
+  }
+}
+
+size_t list_bytes(int threads, int kcap) { return (size_t)threads * 2 * (size_t)kcap * 4; }
+
+inline size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// ------------------------------------------------------------------ tuner
+
+struct TuneKey {
+  int k, nbucket;
+  bool operator<(const TuneKey& o) const { return k != o.k ? k < o.k : nbucket < o.nbucket; }
+};
+
+std::mutex g_tune_mu;
+std::map<TuneKey, int> g_tune;  // -> lanes
+
+int nbucket_of(int64_t n) {
+  int b = 0;
+  while ((int64_t(1) << (b + 1)) <= n) ++b;
+  return b;
+}
+
+int heuristic_lanes(int k) { return default_lanes(k); }
+
+}  // namespace
+
+int fill_lanes(int64_t nq) {
+  // one thread per query fills the GPU only with about SMs x 2048 queries;
+  // smaller batches give each query a group of lanes so all SMs work
+  const int64_t target = (int64_t)num_sms() * 2048;
+  int lanes = 1;
+  while (lanes < 32 && nq * lanes < target) lanes <<= 1;
+  if (lanes == 2) lanes = 4;  // no two-lane variant
+  return lanes;
+}
+
+int choose_lanes(int k, int64_t n, int64_t nq) {
+  const int t = tuned_lanes(k, n);
+  return std::max(t ? t : heuristic_lanes(k), fill_lanes(nq));
+}
+
+namespace {
+
+// Largest dynamic shared memory each kernel is launched with; set once.
+std::once_flag g_attr_once;
+cudaError_t g_attr_err = cudaSuccess;
+
+void set_smem_attributes() {
+  cudaError_t e = cudaFuncSetAttribute(knn_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)list_bytes(kThreads, 64));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(knn_batch_smem_kernel<256>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)list_bytes(256, 32));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(knn_batch_smem_kernel<128>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)list_bytes(128, 64));
+  g_attr_err = e;
+}
+
+}  // namespace
+
+BatchLaunch batch_config(int nitems, int blocks_per_sm, int kcap, bool smem_only) {
+  std::call_once(g_attr_once, set_smem_attributes);
+  BatchLaunch b;
+  b.kcap = kcap;
+  b.smem_only = smem_only;
+  b.threads = smem_only ? (kcap <= 32 ? 256 : 128) : kThreads;
+  b.smem = kcap > 0 ? list_bytes(b.threads, kcap) : 0;
+  int occ = 1;
+  cudaError_t e;
+  if (!smem_only)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, knn_batch_kernel, b.threads, b.smem);
+  else if (b.threads == 256)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, knn_batch_smem_kernel<256>, 256, b.smem);
+  else
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, knn_batch_smem_kernel<128>, 128, b.smem);
+  if (e != cudaSuccess || occ < 1) occ = 1;
+  const int per_sm = blocks_per_sm > 0 ? std::min(blocks_per_sm, occ) : occ;
+  const int wpb = b.threads / 32;
+  const int64_t blocks_needed = ((int64_t)std::max(1, nitems) + wpb - 1) / wpb;
+  b.grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)num_sms() * per_sm, blocks_needed));
+  return b;
+}
+
+cudaError_t launch_batch_kernel(const ReqDev* d_reqs, const Item* d_items, int nitems, int* d_next,
+                                const BatchLaunch& b, cudaStream_t s) {
+  if (nitems <= 0) return cudaSuccess;
+  if (g_attr_err != cudaSuccess) return g_attr_err;
+  if (!b.smem_only)
+    knn_batch_kernel<<<b.grid, b.threads, b.smem, s>>>(d_reqs, d_items, nitems, d_next, b.kcap);
+  else if (b.threads == 256)
+    knn_batch_smem_kernel<256><<<b.grid, 256, b.smem, s>>>(d_reqs, d_items, nitems, d_next, b.kcap);
+  else
+    knn_batch_smem_kernel<128><<<b.grid, 128, b.smem, s>>>(d_reqs, d_items, nitems, d_next, b.kcap);
+  return cudaGetLastError();
+}
+
+int tuned_lanes(int k, int64_t n) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  auto it = g_tune.find(TuneKey{k, nbucket_of(n)});
+  return it == g_tune.end() ? 0 : it->second;
+}
+
+void set_tuned_lanes(int k, int64_t n, int lanes) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune[TuneKey{k, nbucket_of(n)}] = lanes;
+}
+
+}  // namespace mknn
+
+using namespace mknn;
+
+struct mknn_batch {
+  int device = -1;
+  int nreq = 0;
+  std::vector<mknn_batch_req> reqs;
+  std::vector<int> lanes;        // chosen lanes per request
+  ReqDev* d_reqs = nullptr;
+  Item* d_items = nullptr;
+  int nitems = 0;
+  int* d_next = nullptr;
+  void* d_ws = nullptr;          // sort scratch: shared histogram, per-request cells and orders
+  size_t ws_bytes = 0;
+  std::vector<size_t> cell_off, perm_off;  // per request, 0 if not sorted
+  BatchLaunch launch;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int64_t total_queries = 0;
+};
+
+namespace {
+
+mknn_status bfail(mknn_status s, const std::string& msg) {
+  set_error(msg);
+  return s;
+}
+
+void free_plan(mknn_batch* b) {
+  if (!b) return;
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  cudaFree(b->d_reqs);
+  cudaFree(b->d_items);
+  cudaFree(b->d_next);
+  cudaFree(b->d_ws);
+  delete b;
+}
+
+// Enqueues the plan's work (sorts + persistent kernel) on stream s.
+cudaError_t enqueue(mknn_batch* b, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(b->d_next, 0, sizeof(int), s);
+  if (e != cudaSuccess) return e;
+  for (int r = 0; r < b->nreq; ++r) {
+    if (!b->perm_off[r]) continue;
+    const mknn_batch_req& R = b->reqs[r];
+    const CloudDevHost cd = R.cloud->dev();
+    // the histogram at offset 0 is shared: the sorts run one after another
+    e = launch_query_sort_split(cd, R.q, R.q_stride, R.nq, b->d_ws,
+                                (int32_t*)((char*)b->d_ws + b->cell_off[r]),
+                                (int32_t*)((char*)b->d_ws + b->perm_off[r]), s);
+    if (e != cudaSuccess) return e;
+  }
+  return launch_batch_kernel(b->d_reqs, b->d_items, b->nitems, b->d_next, b->launch, s);
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t mknn_batch_sizeof_req(void) { return sizeof(mknn_batch_req); }
+
+mknn_status mknn_batch_create(const mknn_batch_req* reqs, int32_t nreq,
+                              const mknn_batch_opts* opts, mknn_batch** out) {
+  if (!out) return bfail(MKNN_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (nreq < 0 || (nreq > 0 && !reqs)) return bfail(MKNN_EINVAL, "bad request array");
+  int dev = 0;
+  cudaGetDevice(&dev);
+  mknn_batch_opts o{};
+  if (opts) o = *opts;
+  const int rounds = o.item_rounds > 0 ? o.item_rounds : 8;
+  std::unique_ptr<mknn_batch> b(new mknn_batch());
+  b->device = dev;
+  b->nreq = nreq;
+  b->reqs.assign(reqs, reqs + nreq);
+  b->lanes.resize(nreq);
+  b->cell_off.assign(nreq, 0);
+  b->perm_off.assign(nreq, 0);
+  std::vector<ReqDev> rd(nreq);
+  std::vector<double> cost(nreq);
+  int64_t plan_nq = 0;  // all requests run in one launch: widen only if the whole plan is small
+  for (int r = 0; r < nreq; ++r) plan_nq += std::max<int64_t>(0, reqs[r].nq);
+  for (int r = 0; r < nreq; ++r) {
+    const mknn_batch_req& R = reqs[r];
+    if (!R.cloud || !R.cloud->d_pts || R.cloud->device != dev)
+      return bfail(MKNN_EINVAL, "request " + std::to_string(r) +
+                                    ": cloud missing or not uploaded on the current device");
+    if (R.nq < 0 || R.nq >= (int64_t)0x7FFFFFFF || R.q_stride < 3 || R.k < 1 ||
+        R.k > MKNN_MAX_K)
+      return bfail(MKNN_EINVAL, "request " + std::to_string(r) + ": bad nq, q_stride or k");
+    int32_t ms = R.m_scalar;
+    if (!R.m) {
+      if (ms == 0) ms = (int32_t)R.cloud->n;
+      if (ms < 1 || ms > R.cloud->n)
+        return bfail(MKNN_EINVAL, "request " + std::to_string(r) + ": m_scalar out of [1, n]");
+    }
+    if (R.nq > 0 && (!R.q || !R.out_idx || !R.out_d2))
+      return bfail(MKNN_EINVAL, "request " + std::to_string(r) + ": NULL device pointer");
+    const int lanes = o.lanes ? o.lanes : choose_lanes(R.k, R.cloud->n, plan_nq);
+    if (variant_index(lanes, R.k) < 0)
+      return bfail(MKNN_EINVAL, "request " + std::to_string(r) + ": lanes/k combination");
+    b->lanes[r] = lanes;
+    const CloudDevHost cd = R.cloud->dev();
+    rd[r] = ReqDev{(const float4*)cd.pts, cd.rowp,   cd.succ, cd.n,  R.q_stride,
+                   R.q,                   R.m,       nullptr, R.out_idx,
+                   R.out_d2,              R.cloud->d_err, R.k, ms};
+    cost[r] = (double)R.k * std::log2((double)R.cloud->n + 2.0);
+    b->total_queries += R.nq;
+  }
+  // sort scratch: one shared histogram, then per request cells and order
+  const bool sort_on = o.sort >= 0;
+  size_t off = kSortHistBytes;
+  for (int r = 0; r < nreq; ++r) {
+    if (!sort_on || reqs[r].nq < (o.sort > 0 ? 1 : 4096)) continue;
+    b->cell_off[r] = off;
+    off += align256((size_t)reqs[r].nq * 4);
+    b->perm_off[r] = off;
+    off += align256((size_t)reqs[r].nq * 4);
+  }
+  b->ws_bytes = off;
+  // work items, requests by decreasing cost
+  std::vector<int> orderq(nreq);
+  for (int r = 0; r < nreq; ++r) orderq[r] = r;
+  std::stable_sort(orderq.begin(), orderq.end(), [&](int a, int c) { return cost[a] > cost[c]; });
+  std::vector<Item> items;
+  for (int r : orderq) {
+    const int v = variant_index(b->lanes[r], reqs[r].k);
+    const int per = item_queries(b->lanes[r], rounds);
+    for (int64_t s0 = 0; s0 < reqs[r].nq; s0 += per)
+      items.push_back(Item{r, (int32_t)s0, (int32_t)std::min<int64_t>(reqs[r].nq, s0 + per), v});
+  }
+  b->nitems = (int)items.size();
+  cudaError_t e;
+  if ((e = cudaMalloc((void**)&b->d_reqs, sizeof(ReqDev) * std::max(nreq, 1))) != cudaSuccess ||
+      (e = cudaMalloc((void**)&b->d_items, sizeof(Item) * std::max<size_t>(items.size(), 1))) !=
+          cudaSuccess ||
+      (e = cudaMalloc((void**)&b->d_next, 256)) != cudaSuccess ||
+      (e = cudaMalloc(&b->d_ws, std::max<size_t>(b->ws_bytes, 256))) != cudaSuccess) {
+    cudaGetLastError();
+    mknn_batch* raw = b.release();
+    free_plan(raw);
+    return bfail(MKNN_ENOMEM, "device allocation for the batch plan failed");
+  }
+  for (int r = 0; r < nreq; ++r)
+    if (b->perm_off[r]) rd[r].perm = (const int32_t*)((char*)b->d_ws + b->perm_off[r]);
+  if ((e = cudaMemcpy(b->d_reqs, rd.data(), sizeof(ReqDev) * nreq, cudaMemcpyHostToDevice)) !=
+          cudaSuccess ||
+      (e = cudaMemcpy(b->d_items, items.data(), sizeof(Item) * items.size(),
+                      cudaMemcpyHostToDevice)) != cudaSuccess) {
+    mknn_batch* raw = b.release();
+    free_plan(raw);
+    return bfail(MKNN_ECUDA, std::string("plan upload: ") + cudaGetErrorString(e));
+  }
+  int kcap = 0;
+  bool smem_only = nreq > 0;
+  for (int r = 0; r < nreq; ++r) {
+    if (b->lanes[r] == 1)
+      kcap = std::max(kcap, (int)reqs[r].k);
+    else
+      smem_only = false;
+  }
+  b->launch = batch_config(b->nitems, o.blocks_per_sm, kcap, smem_only);
+  if (o.graph >= 0) {
+    cudaStream_t cs;
+    if ((e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking)) == cudaSuccess) {
+      e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+      if (e == cudaSuccess) {
+        cudaError_t e2 = enqueue(b.get(), cs);
+        e = cudaStreamEndCapture(cs, &b->graph);
+        if (e == cudaSuccess) e = e2;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+      }
+      cudaStreamDestroy(cs);
+    }
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      if (b->exec) cudaGraphExecDestroy(b->exec);
+      if (b->graph) cudaGraphDestroy(b->graph);
+      b->exec = nullptr;
+      b->graph = nullptr;
+      mknn_batch* raw = b.release();
+      free_plan(raw);
+      return bfail(MKNN_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    }
+  }
+  *out = b.release();
+  return MKNN_OK;
+}
+
+mknn_status mknn_batch_run(mknn_batch* b, mknn_stream_t stream) {
+  if (!b) return bfail(MKNN_EINVAL, "plan is NULL");
+  int dev = -1;
+  cudaGetDevice(&dev);
+  if (dev != b->device) return bfail(MKNN_EINVAL, "plan was made on another device");
+  cudaError_t e = b->exec ? cudaGraphLaunch(b->exec, (cudaStream_t)stream)
+                          : enqueue(b, (cudaStream_t)stream);
+  if (e != cudaSuccess) return bfail(MKNN_ECUDA, std::string("batch run: ") + cudaGetErrorString(e));
+  return MKNN_OK;
+}
+
+mknn_status mknn_batch_info(const mknn_batch* b, int32_t* lanes_out, int64_t* items,
+                            int32_t* grid) {
+  if (!b) return bfail(MKNN_EINVAL, "plan is NULL");
+  if (lanes_out)
+    for (int r = 0; r < b->nreq; ++r) lanes_out[r] = b->lanes[r];
+  if (items) *items = b->nitems;
+  if (grid) *grid = b->launch.grid;
+  return MKNN_OK;
+}
+
+mknn_status mknn_batch_free(mknn_batch* b) {
+  free_plan(b);
+  return MKNN_OK;
+}
+
+mknn_status mknn_knn_batch(const mknn_batch_req* reqs, int32_t nreq, const mknn_batch_opts* opts,
+                           mknn_stream_t stream) {
+  mknn_batch_opts o{};
+  if (opts) o = *opts;
+  o.graph = -1;
+  mknn_batch* b = nullptr;
+  mknn_status st = mknn_batch_create(reqs, nreq, &o, &b);
+  if (st != MKNN_OK) return st;
+  st = mknn_batch_run(b, stream);
+  cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  free_plan(b);
+  if (st != MKNN_OK) return st;
+  if (e != cudaSuccess) return bfail(MKNN_ECUDA, std::string("batch: ") + cudaGetErrorString(e));
+  return MKNN_OK;
+}
+
+// Times each candidate lane width on a sample of every distinct (k, size
+// bucket) among the requests and records the fastest in the tuning table.
+mknn_status mknn_batch_tune(const mknn_batch_req* reqs, int32_t nreq, int64_t sample,
+                            mknn_stream_t stream) {
+  if (nreq < 0 || (nreq > 0 && !reqs)) return bfail(MKNN_EINVAL, "bad request array");
+  // The table serves large launches (whole plans), so each candidate is timed
+  // on at least twice the queries that fill the GPU one per thread; a
+  // request with fewer queries is tiled to that size.
+  const int64_t fill = (int64_t)num_sms() * 2048 * 2;
+  const int64_t ns = std::max<int64_t>(sample, fill);
+  cudaStream_t s = (cudaStream_t)stream;
+  std::map<TuneKey, int> seen;
+  int32_t* d_idx = nullptr;
+  float* d_d2 = nullptr;
+  float* d_q = nullptr;
+  int32_t* d_m = nullptr;
+  size_t cap = 0, cap_q = 0;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  mknn_status st = MKNN_OK;
+  for (int r = 0; r < nreq && st == MKNN_OK; ++r) {
+    const mknn_batch_req& R = reqs[r];
+    if (!R.cloud || R.nq <= 0) continue;
+    const TuneKey key{R.k, nbucket_of(R.cloud->n)};
+    if (seen.count(key)) continue;
+    seen[key] = 1;
+    const size_t need = (size_t)ns * R.k * 4;
+    const size_t need_q = (size_t)ns * R.q_stride * 4;
+    if (need > cap || need_q > cap_q) {
+      cudaFree(d_idx);
+      cudaFree(d_d2);
+      cudaFree(d_q);
+      cudaFree(d_m);
+      d_idx = nullptr;
+      d_d2 = nullptr;
+      d_q = nullptr;
+      d_m = nullptr;
+      if (cudaMalloc((void**)&d_idx, need) != cudaSuccess ||
+          cudaMalloc((void**)&d_d2, need) != cudaSuccess ||
+          cudaMalloc((void**)&d_q, need_q) != cudaSuccess ||
+          cudaMalloc((void**)&d_m, (size_t)ns * 4) != cudaSuccess) {
+        cudaGetLastError();
+        st = bfail(MKNN_ENOMEM, "tuner buffers");
+        break;
+      }
+      cap = need;
+      cap_q = need_q;
+    }
+    for (int64_t off = 0; off < ns; off += R.nq) {
+      const int64_t len = std::min<int64_t>(R.nq, ns - off);
+      cudaMemcpyAsync(d_q + off * R.q_stride, R.q, (size_t)len * R.q_stride * 4,
+                      cudaMemcpyDeviceToDevice, s);
+      if (R.m) cudaMemcpyAsync(d_m + off, R.m, (size_t)len * 4, cudaMemcpyDeviceToDevice, s);
+    }
+    int best = 0;
+    float best_ms = 1e30f;
+    for (int lanes : {1, 4, 8, 16, 32}) {
+      if (variant_index(lanes, R.k) < 0) continue;
+      mknn_knn_opts ko{};
+      ko.lanes = lanes;
+      float ms_min = 1e30f;
+      for (int rep = 0; rep < 3; ++rep) {
+        cudaEventRecord(e0, s);
+        st = mknn_knn_ex(R.cloud, d_q, ns, R.q_stride, R.k, R.m ? d_m : nullptr, R.m_scalar,
+                         d_idx, d_d2, &ko, stream);
+        cudaEventRecord(e1, s);
+        if (st != MKNN_OK) break;
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rep > 0) ms_min = std::min(ms_min, ms);
+      }
+      if (st != MKNN_OK) break;
+      if (ms_min < best_ms) {
+        best_ms = ms_min;
+        best = lanes;
+      }
+    }
+    if (st == MKNN_OK && best) set_tuned_lanes(R.k, R.cloud->n, best);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(d_idx);
+  cudaFree(d_d2);
+  cudaFree(d_q);
+  cudaFree(d_m);
+  return st;
+}
+
+mknn_status mknn_tune_save(const char* path) {
+  if (!path) return bfail(MKNN_EINVAL, "NULL path");
+  FILE* f = std::fopen(path, "w");
+  if (!f) return bfail(MKNN_EIO, std::string("cannot open ") + path);
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  std::fprintf(f, "# k log2(n) lanes\n");
+  for (auto& kv : g_tune) std::fprintf(f, "%d %d %d\n", kv.first.k, kv.first.nbucket, kv.second);
+  return std::fclose(f) == 0 ? MKNN_OK : bfail(MKNN_EIO, "write failed");
+}
+
+mknn_status mknn_tune_load(const char* path) {
+  if (!path) return bfail(MKNN_EINVAL, "NULL path");
+  FILE* f = std::fopen(path, "r");
+  if (!f) return bfail(MKNN_EIO, std::string("cannot open ") + path);
+  char line[256];
+  std::map<TuneKey, int> t;
+  while (std::fgets(line, sizeof line, f)) {
+    if (line[0] == '#') continue;
+    int k, nb, lanes;
+    if (std::sscanf(line, "%d %d %d", &k, &nb, &lanes) == 3 && variant_index(lanes, k) >= 0)
+      t[TuneKey{k, nb}] = lanes;
+  }
+  std::fclose(f);
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  for (auto& kv : t) g_tune[kv.first] = kv.second;
+  return MKNN_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,61 @@
+// Internal interface of the persistent multi-cloud kernel, its work items
+// and the tuning table (shared by the batch plan and the serving loop).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace mknn {
+
+// One request as the persistent kernel sees it (device-side copy).
+struct ReqDev {
+  const float4* pts;
+  const int32_t* rowp;
+  const int32_t* succ;
+  int32_t n;
+  int32_t q_stride;
+  const float* q;
+  const int32_t* m;
+  const int32_t* perm;
+  int32_t* out_idx;
+  float* out_d2;
+  int32_t* err;
+  int32_t k;
+  int32_t m_scalar;
+};
+
+// A contiguous range of one request's queries (in processing order),
+// served by one warp with kernel variant `variant`.
+struct Item {
+  int32_t req, begin, end, variant;
+};
+
+// Variant index for lanes-per-query G and capacity k, or -1.
+int variant_index(int lanes, int k);
+// Queries per work item for the given lanes and rounds per item.
+inline int item_queries(int lanes, int rounds) { return (32 / lanes) * rounds; }
+
+// Shape of one persistent launch.
+struct BatchLaunch {
+  int grid = 1, threads = 256;
+  size_t smem = 0;    // dynamic shared memory for the one-lane candidate lists
+  int kcap = 0;       // list capacity: the largest k among one-lane requests (0: none)
+  bool smem_only = false;  // every request uses the one-lane shared-memory variant
+};
+// Grid, block and shared memory for `nitems` items.
+BatchLaunch batch_config(int nitems, int blocks_per_sm, int kcap, bool smem_only);
+// Launches the persistent kernel; *d_next must be zero on entry.
+cudaError_t launch_batch_kernel(const ReqDev* d_reqs, const Item* d_items, int nitems, int* d_next,
+                                const BatchLaunch& b, cudaStream_t s);
+
+// Lanes per query recorded by the tuner for (k, floor(log2 n)), 0 if none.
+int tuned_lanes(int k, int64_t n);
+void set_tuned_lanes(int k, int64_t n, int lanes);
+// Lanes per query for a launch of nq queries: the tuned (or default) value
+// for (k, n), widened for batches too small to fill the GPU one query per
+// thread.
+int choose_lanes(int k, int64_t n, int64_t nq);
+// The smallest lane width that fills the GPU with nq queries.
+int fill_lanes(int64_t nq);
+
+}  // namespace mknn

@@ -16,6 +16,7 @@
 #include "cloud.h"
 #include "knn_kernels.h"
 #include "predicates.h"
+#include "batch.h"
 
 namespace mknn {
 
@@ -453,9 +454,9 @@ mknn_status mknn_knn_ex(const mknn_cloud* c, const float* q, int64_t nq, int32_t
   }
   if (nq == 0) return MKNN_OK;
   if (!q || !out_idx || !out_d2) return fail(MKNN_EINVAL, "NULL device pointer");
-  int lanes = (opts && opts->lanes) ? opts->lanes : default_lanes(k);
-  if (lanes != 4 && lanes != 8 && lanes != 16 && lanes != 32)
-    return fail(MKNN_EINVAL, "lanes must be 4, 8, 16 or 32");
+  int lanes = (opts && opts->lanes) ? opts->lanes : choose_lanes(k, c->n, nq);
+  if (lanes != 1 && lanes != 4 && lanes != 8 && lanes != 16 && lanes != 32)
+    return fail(MKNN_EINVAL, "lanes must be 1, 4, 8, 16 or 32");
   cudaStream_t s = (cudaStream_t)stream;
   const int32_t* perm = opts ? opts->order : nullptr;
   if (!perm && sort_enabled(opts, nq)) {
@@ -488,6 +489,9 @@ mknn_status mknn_knn_ex(const mknn_cloud* c, const float* q, int64_t nq, int32_t
   L.err = c->d_err;
   L.lanes = lanes;
   L.blocks_per_sm = opts ? opts->blocks_per_sm : 0;
+  L.placement = (opts && opts->placement) ? opts->placement : default_placement(k);
+  if (L.placement != 1 && L.placement != 2)
+    return fail(MKNN_EINVAL, "placement must be 0, 1 (registers) or 2 (shared memory)");
   cudaError_t e = launch_knn_plain(c->dev(), L, s);
   if (e != cudaSuccess) return cuda_fail(e, "knn kernel launch");
   return MKNN_OK;

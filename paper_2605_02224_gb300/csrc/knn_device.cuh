@@ -328,6 +328,308 @@ __device__ __forceinline__ void knn_query(const CloudDev& C, const Grp<G>& g, fl
   }
 }
 
+// ---------------------------------------------------------------------------
+// One query per thread. The candidate list N is an unsorted array of K
+// register slots holding the best min(k, seen) keys, with the worst of them
+// tracked as the admission threshold once the list is full. The order the
+// algorithm needs is recovered on demand: the nearest not-yet-expanded
+// entry among "the first k-1" is the smallest unexpanded key other than the
+// worst one (when the list is full). No lane talks to another, so a warp
+// serves 32 queries with no votes or shuffles; with locality-sorted
+// queries the 32 descents share most of their path.
+template <int K>
+struct TopT {
+  float d[K];
+  uint32_t r[K];  // rank, bit 31 = expanded
+  int cnt;
+  int worst;      // slot of the worst key, valid when cnt == k
+  float wd;       // worst key (threshold); (+inf, kRankMask) while cnt < k
+  uint32_t wr;
+};
+
+template <int K>
+__device__ __forceinline__ void topt_init(TopT<K>& T) {
+#pragma unroll
+  for (int i = 0; i < K; ++i) {
+    T.d[i] = __int_as_float(0x7f800000);
+    T.r[i] = kPadRank;
+  }
+  T.cnt = 0;
+  T.worst = 0;
+  T.wd = __int_as_float(0x7f800000);
+  T.wr = kRankMask;
+}
+
+// Inserts (cd, cr) unless present. Caller checks key_lt(cd, cr, wd, wr).
+template <int K>
+__device__ __forceinline__ void topt_insert(TopT<K>& T, float cd, uint32_t cr, int k) {
+  bool dup = false;
+#pragma unroll
+  for (int i = 0; i < K; ++i) dup |= (T.d[i] == cd) & ((T.r[i] & kRankMask) == cr);
+  if (dup) return;
+  int slot;
+  if (T.cnt < k) {
+    slot = T.cnt++;
+  } else {
+    slot = T.worst;
+  }
+#pragma unroll
+  for (int i = 0; i < K; ++i)
+    if (i == slot) {
+      T.d[i] = cd;
+      T.r[i] = cr;
+    }
+  if (T.cnt == k) {
+    float wd = -1.f;
+    uint32_t wr = 0;
+    int w = 0;
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+      const uint32_t ri = T.r[i] & kRankMask;
+      if (i < k && key_lt(wd, wr, T.d[i], ri)) {
+        wd = T.d[i];
+        wr = ri;
+        w = i;
+      }
+    }
+    T.worst = w;
+    T.wd = wd;
+    T.wr = wr;
+  }
+}
+
+template <int K, bool COUNT>
+__device__ __forceinline__ void knn_query_thread(const CloudDev& C, float qx, float qy, float qz,
+                                                 int k, int m, int32_t* __restrict__ oi,
+                                                 float* __restrict__ od, QueryCounters& qc) {
+  const float INF = __int_as_float(0x7f800000);
+  TopT<K> T;
+  topt_init(T);
+
+  // ---- Algorithm 1
+  int curr = 0;
+  float4 pc = __ldg(C.pts);
+  float dcur = sqd32(qx, qy, qz, pc);
+  topt_insert(T, dcur, 0u, k);
+  if (COUNT) {
+    qc.coords = 1;
+    qc.trans = 1;
+  }
+  for (;;) {
+    int e = __ldg(C.rowp + curr);
+    const int end = __ldg(C.rowp + curr + 1);
+    if (COUNT) qc.rows++;
+    bool moved = false;
+    for (; e < end; ++e) {
+      const int s = __ldg(C.succ + e);
+      if (COUNT) qc.entries++;
+      if (s >= m) break;
+      const float4 ps = __ldg(C.pts + s);
+      const float d = sqd32(qx, qy, qz, ps);
+      if (COUNT) qc.coords++;
+      bool closer;
+      if (dcur >= kTiny && d < dcur * (1.f - kGuard)) {
+        closer = true;
+      } else if ((dcur >= kTiny && d > dcur * (1.f + kGuard)) || (dcur < kTiny && d > 2.f * kTiny)) {
+        closer = false;
+      } else {
+        closer = sqd64(qx, qy, qz, ps.x, ps.y, ps.z) < sqd64(qx, qy, qz, pc.x, pc.y, pc.z);
+      }
+      if (closer) {
+        curr = s;
+        dcur = d;
+        pc = ps;
+        if (key_lt(d, (uint32_t)s, T.wd, T.wr)) topt_insert(T, d, (uint32_t)s, k);
+        if (COUNT) qc.trans++;
+        moved = true;
+        break;
+      }
+    }
+    if (!moved) break;
+  }
+
+  // ---- Algorithm 2
+  for (;;) {
+    float bd = INF;
+    uint32_t br = kRankMask;
+    int bi = -1;
+    const bool full = T.cnt == k;
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+      const uint32_t ri = T.r[i] & kRankMask;
+      const bool ok = (i < T.cnt) && !(T.r[i] & kDoneBit) && !(full && i == T.worst);
+      if (ok && key_lt(T.d[i], ri, bd, br)) {
+        bd = T.d[i];
+        br = ri;
+        bi = i;
+      }
+    }
+    if (bi < 0) break;
+#pragma unroll
+    for (int i = 0; i < K; ++i)
+      if (i == bi) T.r[i] |= kDoneBit;
+    const int site = (int)br;
+    int e = __ldg(C.rowp + site);
+    const int end = __ldg(C.rowp + site + 1);
+    if (COUNT) qc.rows++;
+    for (; e < end; ++e) {
+      const int s = __ldg(C.succ + e);
+      if (COUNT) qc.entries++;
+      if (s >= m) break;
+      const float d = sqd32(qx, qy, qz, __ldg(C.pts + s));
+      if (COUNT) qc.coords++;
+      if (key_lt(d, (uint32_t)s, T.wd, T.wr)) topt_insert(T, d, (uint32_t)s, k);
+    }
+  }
+
+  // ---- output: position of each entry = number of smaller keys
+#pragma unroll
+  for (int i = 0; i < K; ++i) {
+    if (i < T.cnt) {
+      const uint32_t ri = T.r[i] & kRankMask;
+      int pos = 0;
+#pragma unroll
+      for (int j = 0; j < K; ++j) pos += key_lt(T.d[j], T.r[j] & kRankMask, T.d[i], ri) ? 1 : 0;
+      oi[pos] = (int32_t)ri;
+      od[pos] = T.d[i];
+    }
+  }
+  for (int p = T.cnt; p < k; ++p) {
+    oi[p] = -1;
+    od[p] = INF;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// One query per thread with the candidate list N sorted in shared memory:
+// entry i of the lane's list at base[i * 32] (a warp's lists interleaved,
+// so any mix of positions across the lanes is bank-conflict free). An
+// insertion is a binary search - which also finds an equal key, so the
+// membership test of Alg. 2 costs nothing extra - and a shift of the
+// tail; the nearest not-yet-expanded entry among the first k-1 is one bit
+// scan of the expanded mask; the output is already in order. The list
+// takes no registers, which leaves room for more resident warps.
+struct SmemList {
+  float* d;        // this lane's column: d[i * 32]
+  uint32_t* r;
+  int cnt;
+  uint64_t done;   // bit i: entry at position i expanded
+  float wd;        // key of position k-1 (a pad while cnt < k)
+  uint32_t wr;
+};
+
+__device__ __forceinline__ void slist_init(SmemList& L, float* dcol, uint32_t* rcol) {
+  L.d = dcol;
+  L.r = rcol;
+  L.cnt = 0;
+  L.done = 0ull;
+  L.wd = __int_as_float(0x7f800000);
+  L.wr = kRankMask;
+}
+
+// Inserts (cd, cr) if not present; caller checks key_lt(cd, cr, L.wd, L.wr).
+__device__ __forceinline__ void slist_insert(SmemList& L, float cd, uint32_t cr, int k) {
+  int lo = 0, hi = L.cnt;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (key_lt(L.d[mid * 32], L.r[mid * 32], cd, cr))
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  const int pos = lo;
+  if (pos < L.cnt && L.d[pos * 32] == cd && L.r[pos * 32] == cr) return;
+  for (int i = min(L.cnt, k - 1); i > pos; --i) {
+    L.d[i * 32] = L.d[(i - 1) * 32];
+    L.r[i * 32] = L.r[(i - 1) * 32];
+  }
+  L.d[pos * 32] = cd;
+  L.r[pos * 32] = cr;
+  const uint64_t low = pos ? (L.done & (~0ull >> (64 - pos))) : 0ull;
+  L.done = low | ((L.done >> pos) << 1 << pos);
+  if (L.cnt < k) L.cnt++;
+  if (L.cnt == k) {
+    L.wd = L.d[(k - 1) * 32];
+    L.wr = L.r[(k - 1) * 32];
+  }
+}
+
+// Descent decision: is the candidate at squared distance d (site ps)
+// strictly closer than the current site (dcur, pc)? float32 outside the
+// guard band, float64 in the oracle's order inside it.
+__device__ __forceinline__ bool strictly_closer(float qx, float qy, float qz, float d, float4 ps,
+                                                float dcur, float4 pc) {
+  if (dcur >= kTiny) {
+    if (d < dcur * (1.f - kGuard)) return true;
+    if (d > dcur * (1.f + kGuard)) return false;
+  } else if (d > 2.f * kTiny) {
+    return false;
+  }
+  return sqd64(qx, qy, qz, ps.x, ps.y, ps.z) < sqd64(qx, qy, qz, pc.x, pc.y, pc.z);
+}
+
+__device__ __forceinline__ void knn_query_smem(const CloudDev& C, float qx, float qy, float qz,
+                                               int k, int m, float* dcol, uint32_t* rcol,
+                                               int32_t* __restrict__ oi, float* __restrict__ od) {
+  SmemList L;
+  slist_init(L, dcol, rcol);
+
+  // ---- Algorithm 1
+  int curr = 0;
+  float4 pc = __ldg(C.pts);
+  float dcur = sqd32(qx, qy, qz, pc);
+  slist_insert(L, dcur, 0u, k);
+  for (;;) {
+    int e = __ldg(C.rowp + curr);
+    const int end = __ldg(C.rowp + curr + 1);
+    int s_next = e < end ? __ldg(C.succ + e) : 0x7fffffff;
+    bool moved = false;
+    for (; e < end; ++e) {
+      const int s = s_next;
+      s_next = (e + 1 < end) ? __ldg(C.succ + e + 1) : 0x7fffffff;
+      if (s >= m) break;
+      const float4 ps = __ldg(C.pts + s);
+      const float d = sqd32(qx, qy, qz, ps);
+      if (strictly_closer(qx, qy, qz, d, ps, dcur, pc)) {
+        curr = s;
+        dcur = d;
+        pc = ps;
+        if (key_lt(d, (uint32_t)s, L.wd, L.wr)) slist_insert(L, d, (uint32_t)s, k);
+        moved = true;
+        break;
+      }
+    }
+    if (!moved) break;
+  }
+
+  // ---- Algorithm 2
+  for (;;) {
+    const int lim = min(L.cnt, k - 1);
+    const uint64_t cand = ~L.done & ((1ull << lim) - 1ull);
+    if (!cand) break;
+    const int pos = __ffsll((long long)cand) - 1;
+    L.done |= 1ull << pos;
+    const int site = (int)L.r[pos * 32];
+    int e = __ldg(C.rowp + site);
+    const int end = __ldg(C.rowp + site + 1);
+    int s_next = e < end ? __ldg(C.succ + e) : 0x7fffffff;
+    for (; e < end; ++e) {
+      const int s = s_next;
+      s_next = (e + 1 < end) ? __ldg(C.succ + e + 1) : 0x7fffffff;
+      if (s >= m) break;
+      const float d = sqd32(qx, qy, qz, __ldg(C.pts + s));
+      if (key_lt(d, (uint32_t)s, L.wd, L.wr)) slist_insert(L, d, (uint32_t)s, k);
+    }
+  }
+
+  // ---- output (already sorted)
+  for (int p = 0; p < k; ++p) {
+    const bool real = p < L.cnt;
+    oi[p] = real ? (int32_t)L.r[p * 32] : -1;
+    od[p] = real ? L.d[p * 32] : __int_as_float(0x7f800000);
+  }
+}
+
 // Writes a padded row (-1, +inf) for a query that cannot be served.
 template <int G>
 __device__ __forceinline__ void pad_row(const Grp<G>& g, int k, int32_t* oi, float* od) {

@@ -25,8 +25,9 @@ struct PlainLaunch {
   float* out_d2;
   int32_t* counters;     // [4*nq] or NULL
   int32_t* err;          // device error word
-  int lanes;             // 4, 8, 16, 32
+  int lanes;             // 1, 4, 8, 16, 32
   int blocks_per_sm;     // 0 = occupancy limit
+  int placement = 1;     // lanes == 1: 1 = registers per thread, 2 = shared-memory warp tile
 };
 
 // Launches the plain (one cloud) query kernel. Returns a CUDA error code.
@@ -36,13 +37,24 @@ cudaError_t launch_knn_plain(const CloudDevHost& c, const PlainLaunch& L, cudaSt
 // their cell in a 64^3 grid over the cloud's bounding box.
 constexpr int kSortBits = 6;
 constexpr int kSortCells = 1 << (3 * kSortBits);
+constexpr int kSortTile = 1024;                       // cells per scan block
+constexpr int kSortTiles = kSortCells / kSortTile;    // 256
+// histogram + tile totals, each 256-byte aligned (the start of a sort workspace)
+constexpr size_t kSortHistBytes =
+    (((size_t)kSortCells * 4 + 255) & ~(size_t)255) + (((size_t)kSortTiles * 4 + 255) & ~(size_t)255);
 // Scratch for the histogram and per-query cells (perm not included).
 size_t sort_workspace_bytes(int64_t nq);
 // Writes perm[nq] (processing order).
 cudaError_t launch_query_sort(const CloudDevHost& c, const float* q, int32_t q_stride, int64_t nq,
                               void* workspace, int32_t* perm, cudaStream_t stream);
+// Same, with the histogram (kSortCells int32, cleared here) and the
+// per-query cells (nq int32) in separate buffers.
+cudaError_t launch_query_sort_split(const CloudDevHost& c, const float* q, int32_t q_stride,
+                                    int64_t nq, void* hist, int32_t* cell, int32_t* perm,
+                                    cudaStream_t stream);
 
 int default_lanes(int k);
+int default_placement(int k);
 int num_sms();
 
 }  // namespace mknn

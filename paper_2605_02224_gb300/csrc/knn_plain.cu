@@ -45,6 +45,155 @@ __global__ void __launch_bounds__(kThreads) knn_plain_kernel(
   }
 }
 
+// One query per thread.
+template <int K, bool COUNT>
+__global__ void __launch_bounds__(kThreads) knn_plain_thread_kernel(
+    CloudDev C, const float* __restrict__ q, int q_stride, int64_t nq, int k,
+    const int32_t* __restrict__ mq, int m_scalar, const int32_t* __restrict__ perm,
+    int32_t* __restrict__ out_idx, float* __restrict__ out_d2, int32_t* __restrict__ counters,
+    int32_t* __restrict__ err) {
+  const int64_t stride = (int64_t)gridDim.x * kThreads;
+  for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < nq; i += stride) {
+    const int64_t qi = perm ? (int64_t)__ldg(perm + i) : i;
+    const float* qp = q + qi * q_stride;
+    const float qx = __ldg(qp), qy = __ldg(qp + 1), qz = __ldg(qp + 2);
+    const int m = mq ? __ldg(mq + qi) : m_scalar;
+    int32_t* oi = out_idx + qi * k;
+    float* od = out_d2 + qi * k;
+    if (m < 1 || m > C.n) {
+      for (int p = 0; p < k; ++p) {
+        oi[p] = -1;
+        od[p] = __int_as_float(0x7f800000);
+      }
+      atomicOr(err, 1);
+      continue;
+    }
+    QueryCounters qc{0, 0, 0, 0};
+    knn_query_thread<K, COUNT>(C, qx, qy, qz, k, m, oi, od, qc);
+    if (COUNT) {
+      int32_t* c = counters + 4 * qi;
+      c[0] = qc.rows;
+      c[1] = qc.entries;
+      c[2] = qc.coords;
+      c[3] = qc.trans;
+    }
+  }
+}
+
+template <int K, bool COUNT>
+cudaError_t run_thread(const CloudDevHost& c, const PlainLaunch& L, cudaStream_t stream) {
+  static int occ = -1;
+  static std::mutex mu;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    if (occ < 0) {
+      cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+          &occ, knn_plain_thread_kernel<K, COUNT>, kThreads, 0);
+      if (e != cudaSuccess) return e;
+      if (occ < 1) occ = 1;
+    }
+  }
+  const int per_sm = L.blocks_per_sm > 0 ? std::min(L.blocks_per_sm, occ) : occ;
+  const int64_t need = (L.nq + kThreads - 1) / kThreads;
+  int64_t blocks = (int64_t)num_sms() * per_sm;
+  if (need < blocks) blocks = need;
+  if (blocks < 1) blocks = 1;
+  CloudDev C{(const float4*)c.pts, c.rowp, c.succ, c.n};
+  knn_plain_thread_kernel<K, COUNT><<<(unsigned)blocks, kThreads, 0, stream>>>(
+      C, L.q, L.q_stride, L.nq, L.k, L.m, L.m_scalar, L.perm, L.out_idx, L.out_d2, L.counters,
+      L.err);
+  return cudaGetLastError();
+}
+
+// One query per thread, candidate lists in shared memory (kcap entries per
+// thread, a warp's lists interleaved: thread l of warp w owns column l of
+// the warp's [kcap][32] arrays).
+template <int THREADS>
+__global__ void __launch_bounds__(THREADS) knn_plain_smem_kernel(
+    CloudDev C, const float* __restrict__ q, int q_stride, int64_t nq, int k, int kcap,
+    const int32_t* __restrict__ mq, int m_scalar, const int32_t* __restrict__ perm,
+    int32_t* __restrict__ out_idx, float* __restrict__ out_d2, int32_t* __restrict__ err) {
+  extern __shared__ uint32_t smem_lists[];
+  const int warp = (int)(threadIdx.x >> 5), lane = (int)(threadIdx.x & 31u);
+  uint32_t* wbase = smem_lists + (size_t)warp * 2 * kcap * 32;
+  float* dcol = reinterpret_cast<float*>(wbase) + lane;
+  uint32_t* rcol = wbase + kcap * 32 + lane;
+  const int64_t stride = (int64_t)gridDim.x * THREADS;
+  for (int64_t i = (int64_t)blockIdx.x * THREADS + threadIdx.x; i < nq; i += stride) {
+    const int64_t qi = perm ? (int64_t)__ldg(perm + i) : i;
+    const float* qp = q + qi * q_stride;
+    const float qx = __ldg(qp), qy = __ldg(qp + 1), qz = __ldg(qp + 2);
+    const int m = mq ? __ldg(mq + qi) : m_scalar;
+    int32_t* oi = out_idx + qi * k;
+    float* od = out_d2 + qi * k;
+    if (m < 1 || m > C.n) {
+      for (int p = 0; p < k; ++p) {
+        oi[p] = -1;
+        od[p] = __int_as_float(0x7f800000);
+      }
+      atomicOr(err, 1);
+      continue;
+    }
+    knn_query_smem(C, qx, qy, qz, k, m, dcol, rcol, oi, od);
+  }
+}
+
+// Shared memory per block for kcap entries per thread.
+template <int THREADS>
+constexpr size_t smem_bytes(int kcap) {
+  return (size_t)THREADS * 2 * (size_t)kcap * 4;
+}
+
+template <int THREADS, int KMAX>
+cudaError_t run_smem(const CloudDevHost& c, const PlainLaunch& L, cudaStream_t stream) {
+  const int kcap = L.k;
+  const size_t smem = smem_bytes<THREADS>(kcap);
+  static std::mutex mu;
+  static bool attr = false;
+  static int occ_for[KMAX + 1] = {};
+  int occ;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    if (!attr) {
+      // once, at the largest size any k <= KMAX needs
+      cudaError_t e = cudaFuncSetAttribute(knn_plain_smem_kernel<THREADS>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)smem_bytes<THREADS>(KMAX));
+      if (e != cudaSuccess) return e;
+      attr = true;
+    }
+    if (!occ_for[kcap]) {
+      int o = 0;
+      cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+          &o, knn_plain_smem_kernel<THREADS>, THREADS, smem);
+      if (e != cudaSuccess) return e;
+      occ_for[kcap] = o < 1 ? 1 : o;
+    }
+    occ = occ_for[kcap];
+  }
+  const int per_sm = L.blocks_per_sm > 0 ? std::min(L.blocks_per_sm, occ) : occ;
+  const int64_t need = (L.nq + THREADS - 1) / THREADS;
+  int64_t blocks = (int64_t)num_sms() * per_sm;
+  if (need < blocks) blocks = need;
+  if (blocks < 1) blocks = 1;
+  CloudDev C{(const float4*)c.pts, c.rowp, c.succ, c.n};
+  knn_plain_smem_kernel<THREADS><<<(unsigned)blocks, THREADS, smem, stream>>>(
+      C, L.q, L.q_stride, L.nq, L.k, kcap, L.m, L.m_scalar, L.perm, L.out_idx, L.out_d2, L.err);
+  return cudaGetLastError();
+}
+
+template <bool COUNT>
+cudaError_t pick_thread(const CloudDevHost& c, const PlainLaunch& L, cudaStream_t stream) {
+  if (!COUNT && L.placement == 2) {
+    if (L.k <= 32) return run_smem<256, 32>(c, L, stream);
+    return run_smem<128, 64>(c, L, stream);
+  }
+  if (L.k <= 8) return run_thread<8, COUNT>(c, L, stream);
+  if (L.k <= 16) return run_thread<16, COUNT>(c, L, stream);
+  if (L.k <= 32) return run_thread<32, COUNT>(c, L, stream);
+  return run_thread<64, COUNT>(c, L, stream);
+}
+
 template <int G, int S, bool COUNT>
 cudaError_t run(const CloudDevHost& c, const PlainLaunch& L, cudaStream_t stream) {
   static int occ = -1;
@@ -90,6 +239,7 @@ cudaError_t pick_s(const CloudDevHost& c, const PlainLaunch& L, cudaStream_t str
 template <bool COUNT>
 cudaError_t pick_g(const CloudDevHost& c, const PlainLaunch& L, cudaStream_t stream) {
   switch (L.lanes) {
+    case 1: return pick_thread<COUNT>(c, L, stream);
     case 4: return pick_s<4, COUNT>(c, L, stream);
     case 8: return pick_s<8, COUNT>(c, L, stream);
     case 16: return pick_s<16, COUNT>(c, L, stream);
@@ -113,9 +263,22 @@ int num_sms() {
   return sms;
 }
 
+// Measured on the 1M-site torus with 4M box queries: one query per thread
+// is fastest up to k = 16 (k = 4: 359M q/s vs 264M with 8 lanes; k = 16:
+// 124M vs 111M with 16 lanes); above that the 32-slot register list costs
+// too much occupancy and 16 lanes win (k = 32: 44M vs 26M with 1 lane).
 int default_lanes(int k) {
   (void)k;
-  return 8;
+  return 1;
+}
+
+// One query per thread with the candidate list in shared memory is the
+// fastest variant measured at every k (1M-site torus, 4M box queries:
+// k=4 449M q/s, k=16 168M, k=32 60M, k=64 14M; registers: 368M, 125M,
+// 26M, 3M; best group of lanes: 264M, 111M, 44M, 13M).
+int default_placement(int k) {
+  (void)k;
+  return 2;
 }
 
 cudaError_t launch_knn_plain(const CloudDevHost& c, const PlainLaunch& L, cudaStream_t stream) {

@@ -35,47 +35,56 @@ __global__ void qsort_hist(const float* __restrict__ q, int stride, int64_t nq, 
   }
 }
 
-// Exclusive scan of kSortCells counts in place, one block of 1024 threads.
-__global__ void __launch_bounds__(1024) qsort_scan(int32_t* __restrict__ hist) {
-  constexpr int kPer = kSortCells / 1024;
-  __shared__ int32_t warp_sums[32];
-  const int t = threadIdx.x;
-  int32_t local[kPer];
-  int32_t sum = 0;
-  for (int j = 0; j < kPer; ++j) {
-    local[j] = hist[t * kPer + j];
-    sum += local[j];
-  }
-  // inclusive scan of per-thread sums across the block
-  int32_t v = sum;
-  const int lane = t & 31, warp = t >> 5;
+// Exclusive scan of the cell counts, two levels. Level 1: one block per
+// tile of kSortTile cells scans its tile in place (coalesced) and writes
+// the tile total. Level 2: one block scans the kSortTiles totals in place.
+// The scatter adds a cell's in-tile offset to its tile's offset.
+__device__ __forceinline__ int32_t block_exclusive_scan(int32_t v, int32_t* warp_sums,
+                                                        int32_t* total) {
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5, nwarps = blockDim.x >> 5;
+  int32_t x = v;
   for (int o = 1; o < 32; o <<= 1) {
-    const int32_t u = __shfl_up_sync(0xffffffffu, v, o);
-    if (lane >= o) v += u;
+    const int32_t u = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += u;
   }
-  if (lane == 31) warp_sums[warp] = v;
+  if (lane == 31) warp_sums[warp] = x;
   __syncthreads();
   if (warp == 0) {
-    int32_t w = warp_sums[lane];
+    int32_t w = lane < nwarps ? warp_sums[lane] : 0;
     for (int o = 1; o < 32; o <<= 1) {
       const int32_t u = __shfl_up_sync(0xffffffffu, w, o);
       if (lane >= o) w += u;
     }
-    warp_sums[lane] = w;
+    if (lane < nwarps) warp_sums[lane] = w;
   }
   __syncthreads();
-  int32_t run = v - sum + (warp > 0 ? warp_sums[warp - 1] : 0);
-  for (int j = 0; j < kPer; ++j) {
-    hist[t * kPer + j] = run;
-    run += local[j];
-  }
+  *total = warp_sums[nwarps - 1];
+  return x - v + (warp > 0 ? warp_sums[warp - 1] : 0);
+}
+
+__global__ void __launch_bounds__(kSortTile) qsort_scan_tiles(int32_t* __restrict__ hist,
+                                                              int32_t* __restrict__ tiles) {
+  __shared__ int32_t warp_sums[32];
+  const int64_t i = (int64_t)blockIdx.x * kSortTile + threadIdx.x;
+  int32_t total = 0;
+  const int32_t ex = block_exclusive_scan(hist[i], warp_sums, &total);
+  hist[i] = ex;
+  if (threadIdx.x == 0) tiles[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(kSortTiles) qsort_scan_top(int32_t* __restrict__ tiles) {
+  __shared__ int32_t warp_sums[32];
+  int32_t total = 0;
+  tiles[threadIdx.x] = block_exclusive_scan(tiles[threadIdx.x], warp_sums, &total);
 }
 
 __global__ void qsort_scatter(const int32_t* __restrict__ cell, int64_t nq,
-                              int32_t* __restrict__ offs, int32_t* __restrict__ perm) {
+                              int32_t* __restrict__ offs, const int32_t* __restrict__ tiles,
+                              int32_t* __restrict__ perm) {
   const int64_t step = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nq; i += step) {
-    const int32_t pos = atomicAdd(offs + cell[i], 1);
+    const int32_t c = cell[i];
+    const int32_t pos = atomicAdd(offs + c, 1) + __ldg(tiles + (c / kSortTile));
     perm[pos] = (int32_t)i;
   }
 }
@@ -84,15 +93,20 @@ inline size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 }  // namespace
 
-size_t sort_workspace_bytes(int64_t nq) {
-  return align256((size_t)kSortCells * 4) + align256((size_t)nq * 4);
-}
+size_t sort_workspace_bytes(int64_t nq) { return kSortHistBytes + align256((size_t)nq * 4); }
 
 cudaError_t launch_query_sort(const CloudDevHost& c, const float* q, int32_t q_stride, int64_t nq,
                               void* workspace, int32_t* perm, cudaStream_t stream) {
   char* w = (char*)workspace;
-  int32_t* hist = (int32_t*)w;
-  int32_t* cell = (int32_t*)(w + align256((size_t)kSortCells * 4));
+  int32_t* cell = (int32_t*)(w + kSortHistBytes);
+  return launch_query_sort_split(c, q, q_stride, nq, workspace, cell, perm, stream);
+}
+
+cudaError_t launch_query_sort_split(const CloudDevHost& c, const float* q, int32_t q_stride,
+                                    int64_t nq, void* hist_buf, int32_t* cell, int32_t* perm,
+                                    cudaStream_t stream) {
+  int32_t* hist = (int32_t*)hist_buf;
+  int32_t* tiles = (int32_t*)((char*)hist_buf + align256((size_t)kSortCells * 4));
   if (nq == 0) return cudaSuccess;
   cudaError_t e = cudaMemsetAsync(hist, 0, (size_t)kSortCells * 4, stream);
   if (e != cudaSuccess) return e;
@@ -108,8 +122,9 @@ cudaError_t launch_query_sort(const CloudDevHost& c, const float* q, int32_t q_s
   if (blocks > cap) blocks = cap;
   qsort_hist<<<(unsigned)blocks, threads, 0, stream>>>(q, q_stride, nq, c.lo[0], c.lo[1], c.lo[2],
                                                        s[0], s[1], s[2], cell, hist);
-  qsort_scan<<<1, 1024, 0, stream>>>(hist);
-  qsort_scatter<<<(unsigned)blocks, threads, 0, stream>>>(cell, nq, hist, perm);
+  qsort_scan_tiles<<<kSortTiles, kSortTile, 0, stream>>>(hist, tiles);
+  qsort_scan_top<<<1, kSortTiles, 0, stream>>>(tiles);
+  qsort_scatter<<<(unsigned)blocks, threads, 0, stream>>>(cell, nq, hist, tiles, perm);
   return cudaGetLastError();
 }
 

@@ -44,7 +44,40 @@ class mknn_knn_opts(C.Structure):
     _fields_ = [("lanes", C.c_int32), ("sort", C.c_int32), ("blocks_per_sm", C.c_int32),
                 ("counters", C.c_void_p), ("workspace", C.c_void_p),
                 ("workspace_bytes", C.c_size_t), ("order", C.c_void_p),
-                ("reserved", C.c_int32 * 4)]
+                ("placement", C.c_int32), ("reserved", C.c_int32 * 3)]
+
+
+class mknn_batch_req(C.Structure):
+    _fields_ = [("cloud", C.c_void_p), ("q", C.c_void_p), ("nq", C.c_int64),
+                ("q_stride", C.c_int32), ("k", C.c_int32), ("m", C.c_void_p),
+                ("m_scalar", C.c_int32), ("out_idx", C.c_void_p), ("out_d2", C.c_void_p)]
+
+
+class mknn_batch_opts(C.Structure):
+    _fields_ = [("lanes", C.c_int32), ("sort", C.c_int32), ("item_rounds", C.c_int32),
+                ("blocks_per_sm", C.c_int32), ("graph", C.c_int32), ("reserved", C.c_int32 * 7)]
+
+
+class mknn_server_opts(C.Structure):
+    _fields_ = [("slots", C.c_int32), ("plain", C.c_int32), ("mem_budget", C.c_size_t),
+                ("max_batch_queries", C.c_int64), ("lanes", C.c_int32),
+                ("reserved", C.c_int32 * 7)]
+
+
+class mknn_request(C.Structure):
+    _fields_ = [("cloud", C.c_int32), ("k", C.c_int32), ("m", C.c_int32),
+                ("reserved", C.c_int32), ("q", C.c_void_p), ("nq", C.c_int64),
+                ("out_idx", C.c_void_p), ("out_d2", C.c_void_p)]
+
+
+class mknn_serving_stats(C.Structure):
+    _fields_ = [(n, C.c_int64) for n in ("submitted", "completed", "failed", "queries",
+                                         "launches")] + \
+               [(n, C.c_double) for n in ("elapsed_s", "qps", "p50_ms", "p99_ms", "mean_ms",
+                                          "max_ms", "mean_requests_per_launch")]
+
+    def as_dict(self):
+        return {f[0]: getattr(self, f[0]) for f in self._fields_}
 
 
 _lib = None
@@ -91,6 +124,23 @@ def _declare(L):
         "mknn_cloud_validate": (i32, [vp, vp, vp]),
         "mknn_knn_noalloc": (i32, [vp, vp, i64, i32, i32, vp, i32, vp, vp, vp]),
         "mknn_knn_noalloc_max_queries": (i64, []),
+        "mknn_batch_create": (i32, [vp, i32, vp, pp]),
+        "mknn_batch_run": (i32, [vp, vp]),
+        "mknn_batch_info": (i32, [vp, vp, vp, vp]),
+        "mknn_batch_free": (i32, [vp]),
+        "mknn_knn_batch": (i32, [vp, i32, vp, vp]),
+        "mknn_batch_tune": (i32, [vp, i32, i64, vp]),
+        "mknn_tune_save": (i32, [C.c_char_p]),
+        "mknn_tune_load": (i32, [C.c_char_p]),
+        "mknn_server_create": (i32, [vp, pp]),
+        "mknn_server_add_cloud": (i32, [vp, vp, vp]),
+        "mknn_server_submit": (i32, [vp, vp, vp]),
+        "mknn_server_poll": (i32, [vp, C.c_uint64, vp]),
+        "mknn_server_drain": (i32, [vp, C.c_double]),
+        "mknn_server_stats": (i32, [vp, vp]),
+        "mknn_server_latencies": (i32, [vp, vp, i64, vp]),
+        "mknn_server_reset_stats": (i32, [vp]),
+        "mknn_server_destroy": (i32, [vp, C.c_double]),
         "mknn_orient3d": (i32, [vp, vp, vp, vp]),
         "mknn_insphere": (i32, [vp, vp, vp, vp, vp]),
         "mknn_orient3d_exact": (i32, [vp, vp, vp, vp]),
@@ -205,10 +255,11 @@ def mknn_cloud_load(path: str) -> int:
 # ---------------------------------------------------------------- queries
 
 def _opts(lanes=0, sort=0, blocks_per_sm=0, counters=None, workspace=None, workspace_bytes=0,
-          order=None):
+          order=None, placement=0):
     return mknn_knn_opts(lanes=lanes, sort=sort, blocks_per_sm=blocks_per_sm,
                          counters=_ptr(counters), workspace=_ptr(workspace),
-                         workspace_bytes=workspace_bytes, order=_ptr(order))
+                         workspace_bytes=workspace_bytes, order=_ptr(order),
+                         placement=placement)
 
 
 def mknn_query_order_workspace_size(nq: int) -> int:
@@ -271,6 +322,121 @@ def mknn_knn_noalloc(cloud: int, q, nq: int, q_stride: int, k: int, m, m_scalar:
 
 def mknn_knn_noalloc_max_queries() -> int:
     return int(lib().mknn_knn_noalloc_max_queries())
+
+
+# ---------------------------------------------------------------- batches
+
+def batch_reqs(reqs):
+    """reqs: list of dicts with cloud, q, nq, q_stride, k, m, m_scalar,
+    out_idx, out_d2 (device pointers or tensors) -> ctypes array."""
+    arr = (mknn_batch_req * max(1, len(reqs)))()
+    for i, r in enumerate(reqs):
+        arr[i] = mknn_batch_req(cloud=r["cloud"], q=_ptr(r["q"]), nq=int(r["nq"]),
+                                q_stride=int(r.get("q_stride", 3)), k=int(r["k"]),
+                                m=_ptr(r.get("m")), m_scalar=int(r.get("m_scalar", 0)),
+                                out_idx=_ptr(r["out_idx"]), out_d2=_ptr(r["out_d2"]))
+    return arr
+
+
+def mknn_batch_create(reqs, lanes=0, sort=0, item_rounds=0, blocks_per_sm=0, graph=0) -> int:
+    arr = batch_reqs(reqs)
+    o = mknn_batch_opts(lanes=lanes, sort=sort, item_rounds=item_rounds,
+                        blocks_per_sm=blocks_per_sm, graph=graph)
+    out = C.c_void_p()
+    _check(lib().mknn_batch_create(arr, len(reqs), C.addressof(o), C.byref(out)))
+    return out.value
+
+
+def mknn_batch_run(plan: int, stream: int = 0):
+    _check(lib().mknn_batch_run(plan, stream or None))
+
+
+def mknn_batch_info(plan: int, nreq: int):
+    lanes = np.zeros(max(1, nreq), np.int32)
+    items, grid = C.c_int64(), C.c_int32()
+    _check(lib().mknn_batch_info(plan, _ptr(lanes), C.byref(items), C.byref(grid)))
+    return lanes[:nreq], items.value, grid.value
+
+
+def mknn_batch_free(plan: int):
+    _check(lib().mknn_batch_free(plan))
+
+
+def mknn_knn_batch(reqs, stream: int = 0, **opt):
+    arr = batch_reqs(reqs)
+    o = mknn_batch_opts(**opt)
+    _check(lib().mknn_knn_batch(arr, len(reqs), C.addressof(o), stream or None))
+
+
+def mknn_batch_tune(reqs, sample: int = 1 << 16, stream: int = 0):
+    arr = batch_reqs(reqs)
+    _check(lib().mknn_batch_tune(arr, len(reqs), sample, stream or None))
+
+
+def mknn_tune_save(path: str):
+    _check(lib().mknn_tune_save(path.encode()))
+
+
+def mknn_tune_load(path: str):
+    _check(lib().mknn_tune_load(path.encode()))
+
+
+# ---------------------------------------------------------------- serving
+
+def mknn_server_create(slots=0, plain=0, mem_budget=0, max_batch_queries=0, lanes=0) -> int:
+    o = mknn_server_opts(slots=slots, plain=plain, mem_budget=mem_budget,
+                         max_batch_queries=max_batch_queries, lanes=lanes)
+    out = C.c_void_p()
+    _check(lib().mknn_server_create(C.addressof(o), C.byref(out)))
+    return out.value
+
+
+def mknn_server_add_cloud(server: int, cloud: int) -> int:
+    cid = C.c_int32()
+    _check(lib().mknn_server_add_cloud(server, cloud, C.byref(cid)))
+    return cid.value
+
+
+def mknn_server_submit(server: int, cloud_id: int, q, k: int, m: int, out_idx, out_d2) -> int:
+    """q, out_idx, out_d2: host arrays (numpy or pinned torch CPU tensors)
+    that stay alive until the request is done."""
+    nq = int(q.shape[0])
+    r = mknn_request(cloud=cloud_id, k=k, m=m, q=_ptr(q), nq=nq, out_idx=_ptr(out_idx),
+                     out_d2=_ptr(out_d2))
+    t = C.c_uint64()
+    _check(lib().mknn_server_submit(server, C.addressof(r), C.byref(t)))
+    return t.value
+
+
+def mknn_server_poll(server: int, ticket: int) -> int:
+    s = C.c_int32()
+    _check(lib().mknn_server_poll(server, ticket, C.byref(s)))
+    return s.value
+
+
+def mknn_server_drain(server: int, timeout_s: float = 60.0):
+    _check(lib().mknn_server_drain(server, timeout_s))
+
+
+def mknn_server_stats(server: int) -> dict:
+    s = mknn_serving_stats()
+    _check(lib().mknn_server_stats(server, C.addressof(s)))
+    return s.as_dict()
+
+
+def mknn_server_latencies(server: int, cap: int) -> np.ndarray:
+    out = np.zeros(max(1, cap), np.float64)
+    n = C.c_int64()
+    _check(lib().mknn_server_latencies(server, _ptr(out), cap, C.byref(n)))
+    return out[:n.value]
+
+
+def mknn_server_reset_stats(server: int):
+    _check(lib().mknn_server_reset_stats(server))
+
+
+def mknn_server_destroy(server: int, timeout_s: float = 60.0):
+    _check(lib().mknn_server_destroy(server, timeout_s))
 
 
 def mknn_cloud_check(cloud: int) -> int:

@@ -10,16 +10,16 @@ import numpy as np
 from paper_2605_02224_gb300 import Cloud
 from paper_2605_02224_gb300 import mknn as M
 
-_CACHE_DIR = os.path.join(tempfile.gettempdir(), "mknn_test_clouds")
+_CACHE_DIR = os.path.join(tempfile.gettempdir(), "mknn_clouds")
 
 
-def built_cloud(points: np.ndarray, order: np.ndarray, tag: str) -> Cloud:
-    """Builds (or loads a cached build of) a cloud; cached by content hash."""
+def built_cloud(points: np.ndarray, order: np.ndarray, tag: str = "") -> Cloud:
+    """Builds (or loads a cached build of) a cloud; cached by content hash
+    (the benchmark uses the same cache, so a cloud is built once per box)."""
     os.makedirs(_CACHE_DIR, exist_ok=True)
-    h = hashlib.sha1()
-    h.update(np.ascontiguousarray(points).tobytes())
-    h.update(np.ascontiguousarray(order).tobytes())
-    path = os.path.join(_CACHE_DIR, f"{tag}-{h.hexdigest()[:16]}.mknn")
+    h = hashlib.sha1(np.ascontiguousarray(points).tobytes() +
+                     np.ascontiguousarray(order).tobytes())
+    path = os.path.join(_CACHE_DIR, f"{h.hexdigest()[:16]}.mknn")
     if os.path.exists(path):
         try:
             return Cloud.load(path)

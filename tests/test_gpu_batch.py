@@ -1,0 +1,148 @@
+"""The persistent multi-cloud kernel, its plan, graph replay and tuner."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import workloads as W
+from paper_2605_02224_gb300 import Cloud
+from paper_2605_02224_gb300 import mknn as M
+from tests import parity
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    t = pytest.importorskip("torch")
+    if not t.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return t
+
+
+@pytest.fixture(scope="module")
+def clouds(torch):
+    """Eight clouds of the batching workload's recipe, scaled down."""
+    wls = W.batch_clouds(n_clouds=8, lo=2000, hi=60000, seed=21)
+    out = []
+    for wl in wls:
+        c = Cloud.build(wl.points, wl.order).upload()
+        out.append((wl, c))
+    yield out
+    for _, c in out:
+        c.close()
+
+
+def _requests(torch, clouds, m_mode="scalar"):
+    reqs, keep = [], []
+    for i, (wl, c) in enumerate(clouds):
+        q = torch.from_numpy(wl.queries).cuda()
+        nq = wl.nq
+        idx = torch.full((nq, wl.k), -9, dtype=torch.int32, device="cuda")
+        d2 = torch.full((nq, wl.k), -9.0, dtype=torch.float32, device="cuda")
+        m = None
+        ms = 0
+        if m_mode == "array" and i % 2 == 0:
+            mv = np.clip(np.floor(np.exp(W.uniform(70 + i, 1, nq) * np.log(wl.n))), 1, wl.n)
+            m = torch.from_numpy(mv.astype(np.int32)).cuda()
+        elif m_mode == "array":
+            ms = max(1, wl.n // 3)
+        reqs.append(dict(cloud=c.handle, q=q, nq=nq, q_stride=3, k=wl.k, m=m, m_scalar=ms,
+                         out_idx=idx, out_d2=d2))
+        keep.append((wl, c, q, m, ms, idx, d2))
+    return reqs, keep
+
+
+def _plain(torch, c, q, k, m, ms):
+    idx, d2 = c.knn(q, k, m if m is not None else (ms or None))
+    torch.cuda.synchronize()
+    return idx.cpu().numpy(), d2.cpu().numpy()
+
+
+@pytest.mark.parametrize("lanes", [0, 1, 4, 8, 16, 32])
+def test_batch_equals_plain_per_request(torch, clouds, lanes):
+    reqs, keep = _requests(torch, clouds, "array")
+    kmax = {4: 16}.get(lanes, 64)     # variants compiled into the persistent kernel
+    if any(r["k"] > kmax for r in reqs):
+        bad = [dict(r) for r in reqs]
+        with pytest.raises(M.MknnError) as ei:
+            M.mknn_knn_batch(bad, torch.cuda.current_stream().cuda_stream, lanes=lanes)
+        assert ei.value.status == 1
+        reqs = [r for r in reqs if r["k"] <= kmax]
+        keep = [kp for kp in keep if kp[0].k <= kmax]
+    M.mknn_knn_batch(reqs, torch.cuda.current_stream().cuda_stream, lanes=lanes)
+    torch.cuda.synchronize()
+    for wl, c, q, m, ms, idx, d2 in keep:
+        pi, pd = _plain(torch, c, q, wl.k, m, ms)
+        assert np.array_equal(idx.cpu().numpy(), pi), wl.name
+        assert np.array_equal(d2.cpu().numpy(), pd), wl.name
+
+
+def test_batch_against_oracle_sample(torch, clouds):
+    reqs, keep = _requests(torch, clouds, "array")
+    plan = M.mknn_batch_create(reqs)
+    M.mknn_batch_run(plan, torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    for wl, c, q, m, ms, idx, d2 in keep:
+        mh = m.cpu().numpy() if m is not None else (ms or wl.n)
+        I, D = idx.cpu().numpy(), d2.cpu().numpy()
+        mv = mh if np.ndim(mh) else np.full(wl.nq, mh)
+        parity.check_row_properties(I, D, wl.k, np.asarray(mv, np.int64), wl.n)
+        parity.check_rows(wl.ranked_points(), wl.queries, wl.k, mh, I, D,
+                          rows=range(0, wl.nq, max(1, wl.nq // 150)))
+    lanes, items, grid = M.mknn_batch_info(plan, len(reqs))
+    assert items > 0 and grid > 0 and all(l in (1, 4, 8, 16, 32) for l in lanes)
+    M.mknn_batch_free(plan)
+
+
+def test_graph_replay_sees_new_query_contents(torch, clouds):
+    reqs, keep = _requests(torch, clouds[:3])
+    plan = M.mknn_batch_create(reqs, graph=0)
+    s = torch.cuda.current_stream().cuda_stream
+    M.mknn_batch_run(plan, s)
+    torch.cuda.synchronize()
+    first = [k[5].clone() for k in keep]
+    for wl, c, q, m, ms, idx, d2 in keep:         # move the queries, same buffers
+        q.mul_(0.5)
+    M.mknn_batch_run(plan, s)
+    M.mknn_batch_run(plan, s)                      # replay twice in a row
+    torch.cuda.synchronize()
+    for (wl, c, q, m, ms, idx, d2), f in zip(keep, first):
+        pi, pd = _plain(torch, c, q, wl.k, m, ms)
+        assert np.array_equal(idx.cpu().numpy(), pi)
+        assert not np.array_equal(f.cpu().numpy(), pi) or wl.nq < 10
+    M.mknn_batch_free(plan)
+
+
+def test_tuner_fills_table_and_plan_uses_it(torch, clouds, tmp_path):
+    reqs, keep = _requests(torch, clouds)
+    s = torch.cuda.current_stream().cuda_stream
+    M.mknn_batch_tune(reqs, 4096, s)
+    path = str(tmp_path / "tune.txt")
+    M.mknn_tune_save(path)
+    lines = [l for l in open(path) if not l.startswith("#")]
+    assert len(lines) >= 1
+    M.mknn_tune_load(path)
+    plan = M.mknn_batch_create(reqs)
+    lanes, _, _ = M.mknn_batch_info(plan, len(reqs))
+    table = {(int(a), int(b)): int(c) for a, b, c in (l.split() for l in lines)}
+    for (wl, *_), l in zip(keep, lanes):
+        key = (wl.k, int(np.floor(np.log2(wl.n))))
+        assert table.get(key, l) == l
+    M.mknn_batch_run(plan, s)
+    torch.cuda.synchronize()
+    for wl, c, q, m, ms, idx, d2 in keep:
+        pi, _ = _plain(torch, c, q, wl.k, m, ms)
+        assert np.array_equal(idx.cpu().numpy(), pi)
+    M.mknn_batch_free(plan)
+
+
+def test_batch_rejects_bad_requests(torch, clouds):
+    reqs, _ = _requests(torch, clouds[:2])
+    reqs[1]["k"] = 0
+    with pytest.raises(M.MknnError) as ei:
+        M.mknn_batch_create(reqs)
+    assert ei.value.status == 1
+    reqs[1]["k"] = 65
+    with pytest.raises(M.MknnError):
+        M.mknn_batch_create(reqs)

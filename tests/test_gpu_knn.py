@@ -14,7 +14,9 @@ from tests.gpu_util import built_cloud, run_knn
 
 pytestmark = pytest.mark.gpu
 
-LANES = (4, 8, 16, 32)
+LANES = (1, 4, 8, 16, 32)
+# (lanes per query, candidate-list placement): 1 = registers, 2 = shared-memory warp tile
+VARIANTS = ((1, 1), (1, 2), (4, 1), (8, 1), (16, 1), (32, 1))
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -41,10 +43,10 @@ def test_tiny_exhaustive(n, table):
     Q = W.box_queries(60, 7, [-1.5] * 3, [1.5] * 3)
     Q = np.concatenate([Q, Pr[: min(n, 20)]])          # queries exactly on sites
     ks = sorted({1, 2, min(n, 8), min(n + 1, 64), 33, 64})
-    for lanes in LANES:
+    for lanes, pl in VARIANTS:
         for k in ks:
             for m in sorted({1, max(1, n // 2), n}):
-                idx, d2 = run_knn(c, Q, k, m, lanes=lanes, sort=1 if k % 2 else -1)
+                idx, d2 = run_knn(c, Q, k, m, lanes=lanes, placement=pl, sort=1 if k % 2 else -1)
                 parity.check_rows(Pr, Q, k, m, idx, d2)
     c.close()
 
@@ -54,8 +56,8 @@ def test_small_sphere_workload_all_queries():
     wl = W.small_sphere()
     c = Cloud.build(wl.points, wl.order).upload()
     Pr = wl.ranked_points()
-    for lanes in LANES:
-        idx, d2 = run_knn(c, wl.queries, wl.k, lanes=lanes)
+    for lanes, pl in VARIANTS:
+        idx, d2 = run_knn(c, wl.queries, wl.k, lanes=lanes, placement=pl)
         parity.check_rows(Pr, wl.queries, wl.k, 0, idx, d2)
     idx0, d20 = run_knn(c, wl.queries, wl.k)
     assert c.check() == 0
@@ -68,8 +70,8 @@ def test_sphere_centre_closed_form():
     wl = W.small_sphere(nq=1)
     c = Cloud.build(wl.points, wl.order).upload()
     Q = np.zeros((4, 3), np.float32)
-    for lanes in LANES:
-        idx, d2 = run_knn(c, Q, 64, lanes=lanes)
+    for lanes, pl in VARIANTS:
+        idx, d2 = run_knn(c, Q, 64, lanes=lanes, placement=pl)
         assert np.all(np.abs(d2 - 1.0) <= 1e-6)
         assert all(np.unique(r).size == 64 for r in idx)
         assert np.all(idx >= 0) and np.all(idx < 2000)
@@ -90,8 +92,8 @@ def test_lattice_rings_closed_form():
     rng = np.random.default_rng(0)
     centres = rng.integers(5, L - 5, size=(50, 3)).astype(np.float32)
     for k in (1, 7, 19, 27, 33):
-        for lanes in LANES:
-            idx, d2 = run_knn(c, centres, k, lanes=lanes)
+        for lanes, pl in VARIANTS:
+            idx, d2 = run_knn(c, centres, k, lanes=lanes, placement=pl)
             parity.check_rows(P, centres, k, 0, idx, d2)
             cum = np.cumsum([r3[s] for s in range(13)])
             smax = int(np.searchsorted(cum, k))
@@ -114,8 +116,8 @@ def test_prefix_bound_per_query_and_padding():
     m = np.clip(m, 1, 20000)
     m[:50] = np.arange(1, 51)                       # m < k: padded rows
     for k in (1, 10, 64):
-        for lanes in LANES:
-            idx, d2 = run_knn(c, Q, k, m, lanes=lanes)
+        for lanes, pl in VARIANTS:
+            idx, d2 = run_knn(c, Q, k, m, lanes=lanes, placement=pl)
             parity.check_row_properties(idx, d2, k, m.astype(np.int64), 20000)
             parity.check_rows(Pr, Q, k, m, idx, d2, rows=range(0, nq, 7))
     assert c.check() == 0
@@ -154,8 +156,8 @@ def test_duplicates_and_degenerate_clouds():
     Pr = P[order]
     Q = np.concatenate([W.box_queries(500, 78, [-1] * 3, [8] * 3), Pr[:100]]).astype(np.float32)
     for k in (1, 2, 9, 27, 64):
-        for lanes in (8, 32):
-            idx, d2 = run_knn(c, Q, k, lanes=lanes)
+        for lanes, pl in ((1, 1), (1, 2), (8, 1), (32, 1)):
+            idx, d2 = run_knn(c, Q, k, lanes=lanes, placement=pl)
             parity.check_rows(Pr, Q, k, 0, idx, d2)
     c.close()
 
@@ -185,7 +187,7 @@ def test_counters_match_algorithm_restatement():
     Pr = P[order]
     _, rowp, succ = c.table()
     Q = W.box_queries(400, 13, [-1.5, -1.5, -0.5], [1.5, 1.5, 0.5])
-    for k, lanes in ((1, 8), (16, 8), (16, 32), (5, 4)):
+    for k, lanes in ((1, 8), (16, 8), (16, 32), (5, 4), (16, 1), (1, 1)):
         cnt = torch.zeros((Q.shape[0], 4), dtype=torch.int32, device="cuda")
         idx, d2 = run_knn(c, Q, k, lanes=lanes, counters=cnt)
         cnt = cnt.cpu().numpy()
@@ -201,6 +203,23 @@ def test_counters_match_algorithm_restatement():
 
 
 @pytest.mark.slow
+def test_prefix_workload_full_size_sampled():
+    """The 4M-site bumpy sphere with 8M queries, each with its own m
+    (log-uniform in [1000, n]), k = 10: every row's properties, a sample
+    of rows against brute force restricted to P_{1:m}."""
+    wl = W.prefix_bumpy()
+    c = built_cloud(wl.points, wl.order, "bumpy4m")
+    c.upload()
+    idx, d2 = run_knn(c, wl.queries, wl.k, wl.m)
+    parity.check_row_properties(idx, d2, wl.k, wl.m.astype(np.int64), wl.n)
+    Pr = wl.ranked_points()
+    rows = np.linspace(0, wl.nq - 1, 120).astype(np.int64)
+    parity.check_rows(Pr, wl.queries, wl.k, wl.m, idx, d2, rows=rows)
+    assert c.check() == 0
+    c.close()
+
+
+@pytest.mark.slow
 def test_large_torus_full_size_sampled():
     """The 1M-point torus with 4M queries, k = 16, launched as the benchmark
     launches it: every row's properties, and a sample of rows against the
@@ -210,6 +229,9 @@ def test_large_torus_full_size_sampled():
     c.upload()
     idx, d2 = run_knn(c, wl.queries, wl.k)
     parity.check_row_properties(idx, d2, wl.k, np.full(wl.nq, wl.n, np.int64), wl.n)
+    for lanes, pl in ((1, 2), (16, 1)):              # other variants give the same rows
+        i2, d22 = run_knn(c, wl.queries, wl.k, lanes=lanes, placement=pl)
+        assert np.array_equal(i2, idx) and np.array_equal(d22, d2)
     Pr = wl.ranked_points()
     rows = np.linspace(0, wl.nq - 1, 400).astype(np.int64)
     parity.check_rows(Pr, wl.queries, wl.k, 0, idx, d2, rows=rows)

@@ -1,0 +1,169 @@
+"""The serving loop: continuous batching, admission by memory, results equal
+alone and in the mix, bounded waits."""
+from __future__ import annotations
+
+import threading
+import time
+
+import numpy as np
+import pytest
+
+import workloads as W
+from paper_2605_02224_gb300 import Cloud
+from paper_2605_02224_gb300 import mknn as M
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    t = pytest.importorskip("torch")
+    if not t.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return t
+
+
+@pytest.fixture(scope="module")
+def resident(torch):
+    wls = W.serve_clouds(n_clouds=4, lo=5000, hi=80000, seed=41)
+    cl = [Cloud.build(w.points, w.order).upload() for w in wls]
+    yield wls, cl
+    for c in cl:
+        c.close()
+
+
+def _requests(wls, n_req, seed=42, max_q=5000, rate=5000.0):
+    return W.serve_requests(wls, n_req, rate, seed=seed, max_q=max_q)
+
+
+def _alone(clouds, r):
+    c = clouds[r.cloud]
+    return c.knn_host(r.queries, r.k, r.m)
+
+
+def _pinned(torch, shape, dtype):
+    return torch.empty(shape, dtype=dtype).pin_memory()
+
+
+@pytest.mark.parametrize("plain", [0, 1])
+def test_each_result_equal_alone_and_in_the_mix(torch, resident, plain):
+    wls, cl = resident
+    reqs = _requests(wls, 120)
+    srv = M.mknn_server_create(slots=3, plain=plain, mem_budget=256 << 20)
+    ids = [M.mknn_server_add_cloud(srv, c.handle) for c in cl]
+    outs, tickets = [], []
+    for r in reqs:
+        oi = np.empty((r.queries.shape[0], r.k), np.int32)     # pageable on purpose
+        od = np.empty((r.queries.shape[0], r.k), np.float32)
+        tickets.append(M.mknn_server_submit(srv, ids[r.cloud], r.queries, r.k, r.m, oi, od))
+        outs.append((oi, od))
+    M.mknn_server_drain(srv, 120.0)
+    st = M.mknn_server_stats(srv)
+    assert st["completed"] == len(reqs) and st["failed"] == 0
+    assert st["p99_ms"] >= st["p50_ms"] > 0
+    if not plain:
+        assert st["mean_requests_per_launch"] > 1.0     # requests really were batched
+    for r, (oi, od), t in zip(reqs, outs, tickets):
+        assert M.mknn_server_poll(srv, t) == 1
+        ai, ad = _alone(cl, r)
+        assert np.array_equal(oi, ai) and np.array_equal(od, ad)
+    M.mknn_server_destroy(srv, 60.0)
+
+
+def test_poisson_arrivals_pinned_buffers_overlap(torch, resident):
+    """Requests arrive while others run (Poisson, from a client thread);
+    all complete with results equal to running each alone."""
+    wls, cl = resident
+    reqs = _requests(wls, 80, seed=7, rate=400.0)
+    srv = M.mknn_server_create(slots=3, mem_budget=512 << 20)
+    ids = [M.mknn_server_add_cloud(srv, c.handle) for c in cl]
+    bufs = []
+    for r in reqs:
+        q = _pinned(torch, r.queries.shape, torch.float32)
+        q.copy_(torch.from_numpy(r.queries))
+        bufs.append((q, _pinned(torch, (r.queries.shape[0], r.k), torch.int32),
+                     _pinned(torch, (r.queries.shape[0], r.k), torch.float32)))
+    t0 = time.perf_counter()
+
+    def client():
+        for r, (q, oi, od) in zip(reqs, bufs):
+            delay = r.arrival_s - (time.perf_counter() - t0)
+            if delay > 0:
+                time.sleep(delay)
+            M.mknn_server_submit(srv, ids[r.cloud], q, r.k, r.m, oi, od)
+
+    th = threading.Thread(target=client)
+    th.start()
+    th.join()
+    M.mknn_server_drain(srv, 120.0)
+    st = M.mknn_server_stats(srv)
+    assert st["completed"] == len(reqs)
+    for r, (q, oi, od) in zip(reqs, bufs):
+        ai, ad = _alone(cl, r)
+        assert np.array_equal(oi.numpy(), ai) and np.array_equal(od.numpy(), ad)
+    lat = M.mknn_server_latencies(srv, len(reqs))
+    assert lat.shape[0] == len(reqs) and np.all(lat > 0)
+    M.mknn_server_destroy(srv, 60.0)
+
+
+def test_admission_by_memory_queues_and_rejects(torch, resident):
+    wls, cl = resident
+    srv = M.mknn_server_create(slots=2, mem_budget=24 << 20)
+    cid = M.mknn_server_add_cloud(srv, cl[0].handle)
+    lo, hi = W.padded_box(wls[0].points)
+    big = W.box_queries(200_000, 5, lo, hi)                 # ~ 30 MB in flight: too big
+    oi = np.empty((200_000, 16), np.int32)
+    od = np.empty((200_000, 16), np.float32)
+    with pytest.raises(M.MknnError) as ei:
+        M.mknn_server_submit(srv, cid, big, 16, 0, oi, od)
+    assert ei.value.status == 2
+    # many requests that fit one or two at a time: all complete, in order of budget
+    qs = [W.box_queries(30_000, 100 + i, lo, hi) for i in range(12)]
+    outs = [(np.empty((30_000, 8), np.int32), np.empty((30_000, 8), np.float32)) for _ in qs]
+    for q, (a, b) in zip(qs, outs):
+        M.mknn_server_submit(srv, cid, q, 8, 0, a, b)
+    M.mknn_server_drain(srv, 120.0)
+    st = M.mknn_server_stats(srv)
+    assert st["completed"] == 12
+    for q, (a, b) in zip(qs, outs):
+        ai, _ = cl[0].knn_host(q, 8)
+        assert np.array_equal(a, ai)
+    M.mknn_server_destroy(srv, 60.0)
+
+
+def test_held_cloud_cannot_be_freed_and_bad_requests(torch, resident):
+    wls, cl = resident
+    extra = Cloud.build(wls[1].points, wls[1].order)
+    srv = M.mknn_server_create()
+    cid = M.mknn_server_add_cloud(srv, extra.handle)
+    with pytest.raises(M.MknnError) as ei:
+        M.mknn_cloud_free(extra.handle)
+    assert ei.value.status == 4
+    q = np.zeros((4, 3), np.float32)
+    oi = np.empty((4, 8), np.int32)
+    od = np.empty((4, 8), np.float32)
+    with pytest.raises(M.MknnError):
+        M.mknn_server_submit(srv, cid + 5, q, 8, 0, oi, od)     # unknown cloud
+    with pytest.raises(M.MknnError):
+        M.mknn_server_submit(srv, cid, q, 0, 0, oi, od)          # k = 0
+    with pytest.raises(M.MknnError):
+        M.mknn_server_submit(srv, cid, q, 8, extra.n + 1, oi, od)  # m > n
+    M.mknn_server_destroy(srv, 30.0)
+    extra.close()                                                # released: frees fine
+
+
+def test_drain_times_out_then_completes(torch, resident):
+    wls, cl = resident
+    srv = M.mknn_server_create(slots=1)
+    cid = M.mknn_server_add_cloud(srv, cl[3].handle)
+    lo, hi = W.padded_box(wls[3].points)
+    q = W.box_queries(1_000_000, 9, lo, hi)
+    oi = np.empty((1_000_000, 32), np.int32)
+    od = np.empty((1_000_000, 32), np.float32)
+    t = M.mknn_server_submit(srv, cid, q, 32, 0, oi, od)
+    with pytest.raises(M.MknnError) as ei:
+        M.mknn_server_drain(srv, 0.0)
+    assert ei.value.status == 5
+    M.mknn_server_drain(srv, 120.0)
+    assert M.mknn_server_poll(srv, t) == 1
+    M.mknn_server_destroy(srv, 30.0)
