@@ -46,7 +46,7 @@ def _args():
     ap.add_argument("--nq", type=int, default=4_000_000)
     ap.add_argument("--k", type=int, default=16)
     ap.add_argument("--placement", type=int, default=0,
-                    help="one-lane candidate lists: 0 default, 1 registers, 2 shared-memory tile")
+                    help="one-lane candidate lists: 0 default, 1 registers, 2 shared memory")
     ap.add_argument("--n", type=int, default=1_000_000)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -220,6 +220,24 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def max_over_ranks(x: float, dist=None, device=None) -> float:
+    """The largest x over all ranks (the slowest rank sets the job time);
+    x itself with no process group."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(total_ms: float, steps: int, nq_per_rank: int, world: int):
+    """(ms per step, whole-job queries/s): every rank answers its own nq
+    queries per step (weak scaling), the job takes the slowest rank's time."""
+    ms_per_step = total_ms / steps
+    return ms_per_step, world * nq_per_rank / (ms_per_step / 1e3)
+
+
 def _build_many(wls, tag):
     """Builds (or loads cached builds of) several clouds in parallel host threads."""
     from concurrent.futures import ThreadPoolExecutor
@@ -349,6 +367,8 @@ def batch_workload(args, M, torch):
                                f"(half box, half near-surface), k in {{1,4,8,16,32}}",
                    "l2": "flushed before every timed step", "items": items, "grid": grid,
                    "lanes_chosen": {str(l): int((lanes == l).sum()) for l in set(lanes.tolist())},
+                   "lanes_by_k": {f"k={w.k}": sorted({int(l) for ww, l in zip(wls, lanes)
+                                                     if ww.k == w.k}) for w in wls},
                    "tune_seconds": tune_s,
                    "build_seconds_max": build_s if build_s is not None else "cached"},
         "plain_one_launch_per_cloud": {"value": nq / (ms_plain / 1e3), "ms_per_step": ms_plain},
@@ -491,14 +511,10 @@ def main():
     clk = clocks.stop()
     step_ms = [e[0].elapsed_time(e[2]) for e in evs]
     kern_ms = [e[1].elapsed_time(e[2]) for e in evs]
-    total_ms = float(sum(step_ms))
+    total_ms = max_over_ranks(float(sum(step_ms)), dist, dev)
     if dist:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
         dist.barrier()
-    ms_per_step = total_ms / args.steps
-    value = world * nq / (ms_per_step / 1e3)
+    ms_per_step, value = job_rate(total_ms, args.steps, nq, world)
 
     # end to end through the host-buffer entry point (pinned host memory)
     qh = torch.from_numpy(wl.queries).pin_memory()
@@ -513,11 +529,7 @@ def main():
         t0 = time.perf_counter()
         M.mknn_knn_host(cloud.handle, qh, k, None, 0, oh_i, oh_d)
         e2e_t.append(time.perf_counter() - t0)
-    e2e_s = float(np.mean(e2e_t))
-    if dist:
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(float(np.mean(e2e_t)), dist, dev)
     agree = bool(torch.equal(oh_i, idx.cpu()))
 
     kern_s = float(np.mean(kern_ms)) / 1e3

@@ -157,7 +157,7 @@ mknn_status mknn_knn(const mknn_cloud* cloud, const float* q, int64_t nq, int32_
 
 /* Tuning knobs of one query launch; zero-initialise for defaults. */
 typedef struct {
-  int32_t lanes;        /* lanes per query: 0 = default, or 4, 8, 16, 32 */
+  int32_t lanes;        /* lanes per query: 0 = default, or 1, 4, 8, 16, 32 */
   int32_t sort;         /* query locality sort: 0 = default, 1 = on, -1 = off */
   int32_t blocks_per_sm;/* 0 = as many as fit */
   int32_t* counters;    /* device int32[4*nq] or NULL: per query rows opened,
@@ -284,7 +284,9 @@ mknn_status mknn_batch_free(mknn_batch* plan);
 mknn_status mknn_knn_batch(const mknn_batch_req* reqs, int32_t nreq, const mknn_batch_opts* opts,
                            mknn_stream_t stream);
 
-/* Autotuner: for every distinct (k, floor(log2 n)) among the requests,
+/* Autotuner: for every distinct (k, floor(log2 n), floor(log2(1 + longest
+ * successor list))) among the requests - the last separates clouds with
+ * hub rows (nearly coplanar sites), whose queries cost far more -
  * times each kernel variant - one query per thread with a shared-memory
  * candidate list (lanes 1), or a group of 4, 8, 16 or 32 lanes with the
  * list in registers - on max(sample, 2 x SMs x 2048) queries of that
@@ -292,10 +294,12 @@ mknn_status mknn_knn_batch(const mknn_batch_req* reqs, int32_t nreq, const mknn_
  * warm-up) and records the fastest in the process-wide tuning table. Plans,
  * plain launches and the server take the table's entry, widened to more
  * lanes when a launch is too small to fill the GPU one query per thread.
+ * If the environment variable MKNN_TUNE_LOG names a file, one line per
+ * timed candidate (k, n, hub bucket, sample, lanes, ms) is appended to it.
  * Synchronises the stream. Errors: EINVAL, ENOMEM, ECUDA. */
 mknn_status mknn_batch_tune(const mknn_batch_req* reqs, int32_t nreq, int64_t sample,
                             mknn_stream_t stream);
-/* Tuning table as text ("k log2n lanes" per line). */
+/* Tuning table as text ("k log2n hub lanes" per line). */
 mknn_status mknn_tune_save(const char* path);
 mknn_status mknn_tune_load(const char* path);
 

@@ -17,6 +17,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <map>
 #include <memory>
 #include <mutex>
@@ -115,16 +116,15 @@ __device__ __forceinline__ void serve_item(const ReqDev& R, const Item& w) {
   }
 }
 
-// All variants. Three resident blocks per SM caps the variants' union at
-// 80 registers (a few bytes of spill in the largest) instead of 118.
+// The group variants (lists in registers). Three resident blocks per SM
+// caps the variants' union at 80 registers (a few bytes of spill in the
+// largest) instead of 118.
 __global__ void __launch_bounds__(kThreads, 3) knn_batch_kernel(const ReqDev* __restrict__ reqs,
                                                              const Item* __restrict__ items,
                                                              int nitems, int* __restrict__ next,
                                                              int kcap) {
   const uint32_t lane = threadIdx.x & 31u;
-  float* dcol = nullptr;
-  uint32_t* rcol = nullptr;
-  if (kcap > 0) smem_columns(kcap, &dcol, &rcol);
+  (void)kcap;  // the group variants keep their lists in registers
   for (;;) {
     int it = 0;
     if (lane == 0) it = atomicAdd(next, 1);
@@ -145,8 +145,7 @@ __global__ void __launch_bounds__(kThreads, 3) knn_batch_kernel(const ReqDev* __
       case 9: serve_item<16, 4>(R, w); break;
       case 10: serve_item<32, 1>(R, w); break;
       case 11: serve_item<32, 2>(R, w); break;
-      case kSmemVariant: serve_item_smem(R, w, dcol, rcol); break;
-      default: break;
+      default: break;  // one-lane items go to knn_batch_smem_kernel
     }
     __syncwarp();
   }
@@ -182,8 +181,11 @@ inline size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 // ------------------------------------------------------------------ tuner
 
 struct TuneKey {
-  int k, nbucket;
-  bool operator<(const TuneKey& o) const { return k != o.k ? k < o.k : nbucket < o.nbucket; }
+  int k, nbucket, hub;
+  bool operator<(const TuneKey& o) const {
+    if (k != o.k) return k < o.k;
+    return nbucket != o.nbucket ? nbucket < o.nbucket : hub < o.hub;
+  }
 };
 
 std::mutex g_tune_mu;
@@ -199,19 +201,24 @@ int heuristic_lanes(int k) { return default_lanes(k); }
 
 }  // namespace
 
-int fill_lanes(int64_t nq) {
-  // one thread per query fills the GPU only with about SMs x 2048 queries;
-  // smaller batches give each query a group of lanes so all SMs work
-  const int64_t target = (int64_t)num_sms() * 2048;
+int fill_lanes(int64_t nq, int k) {
+  // One query per thread fills the GPU with (SMs x resident threads)
+  // queries; resident threads of the shared-memory variant are limited by
+  // its 48 registers (1280 per SM) and by 8 k bytes of list per thread.
+  // Smaller batches give each query a group of lanes so all SMs work.
+  const int64_t per_sm = std::min<int64_t>(1280, 233472 / (8 * (int64_t)std::max(k, 8)));
+  const int64_t target = (int64_t)num_sms() * per_sm;
   int lanes = 1;
   while (lanes < 32 && nq * lanes < target) lanes <<= 1;
   if (lanes == 2) lanes = 4;  // no two-lane variant
   return lanes;
 }
 
-int choose_lanes(int k, int64_t n, int64_t nq) {
-  const int t = tuned_lanes(k, n);
-  return std::max(t ? t : heuristic_lanes(k), fill_lanes(nq));
+int choose_lanes(int k, int64_t n, int hub, int64_t nq) {
+  const int t = tuned_lanes(k, n, hub);
+  int lanes = std::max(t ? t : heuristic_lanes(k), fill_lanes(nq, k));
+  while (lanes < 32 && variant_index(lanes, k) < 0) lanes <<= 1;  // e.g. 4 lanes hold k <= 16
+  return lanes;
 }
 
 namespace {
@@ -272,15 +279,15 @@ cudaError_t launch_batch_kernel(const ReqDev* d_reqs, const Item* d_items, int n
   return cudaGetLastError();
 }
 
-int tuned_lanes(int k, int64_t n) {
+int tuned_lanes(int k, int64_t n, int hub) {
   std::lock_guard<std::mutex> lk(g_tune_mu);
-  auto it = g_tune.find(TuneKey{k, nbucket_of(n)});
+  auto it = g_tune.find(TuneKey{k, nbucket_of(n), hub});
   return it == g_tune.end() ? 0 : it->second;
 }
 
-void set_tuned_lanes(int k, int64_t n, int lanes) {
+void set_tuned_lanes(int k, int64_t n, int hub, int lanes) {
   std::lock_guard<std::mutex> lk(g_tune_mu);
-  g_tune[TuneKey{k, nbucket_of(n)}] = lanes;
+  g_tune[TuneKey{k, nbucket_of(n), hub}] = lanes;
 }
 
 }  // namespace mknn
@@ -293,13 +300,17 @@ struct mknn_batch {
   std::vector<mknn_batch_req> reqs;
   std::vector<int> lanes;        // chosen lanes per request
   ReqDev* d_reqs = nullptr;
-  Item* d_items = nullptr;
-  int nitems = 0;
-  int* d_next = nullptr;
+  // items of the one-lane requests (shared-memory kernel) and of the
+  // group requests (register kernel); each family has its own queue
+  Item* d_items = nullptr;       // [family A items | family B items]
+  int nitems_a = 0, nitems_b = 0;
+  int* d_next = nullptr;         // [0] queue A, [1] queue B
   void* d_ws = nullptr;          // sort scratch: shared histogram, per-request cells and orders
   size_t ws_bytes = 0;
   std::vector<size_t> cell_off, perm_off;  // per request, 0 if not sorted
-  BatchLaunch launch;
+  BatchLaunch launch_a, launch_b;
+  cudaStream_t aux = nullptr;    // second branch when both families are present
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   int64_t total_queries = 0;
@@ -320,12 +331,17 @@ void free_plan(mknn_batch* b) {
   cudaFree(b->d_items);
   cudaFree(b->d_next);
   cudaFree(b->d_ws);
+  if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+  if (b->ev_join) cudaEventDestroy(b->ev_join);
+  if (b->aux) cudaStreamDestroy(b->aux);
   delete b;
 }
 
-// Enqueues the plan's work (sorts + persistent kernel) on stream s.
+// Enqueues the plan's work on stream s: the locality sorts, then the
+// persistent launch of each family present (the two run concurrently on
+// s and the plan's second stream when both are present).
 cudaError_t enqueue(mknn_batch* b, cudaStream_t s) {
-  cudaError_t e = cudaMemsetAsync(b->d_next, 0, sizeof(int), s);
+  cudaError_t e = cudaMemsetAsync(b->d_next, 0, 2 * sizeof(int), s);
   if (e != cudaSuccess) return e;
   for (int r = 0; r < b->nreq; ++r) {
     if (!b->perm_off[r]) continue;
@@ -337,7 +353,21 @@ cudaError_t enqueue(mknn_batch* b, cudaStream_t s) {
                                 (int32_t*)((char*)b->d_ws + b->perm_off[r]), s);
     if (e != cudaSuccess) return e;
   }
-  return launch_batch_kernel(b->d_reqs, b->d_items, b->nitems, b->d_next, b->launch, s);
+  const Item* items_a = b->d_items;
+  const Item* items_b = b->d_items + b->nitems_a;
+  if (b->nitems_a > 0 && b->nitems_b > 0) {
+    if ((e = cudaEventRecord(b->ev_fork, s)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(b->aux, b->ev_fork, 0)) != cudaSuccess) return e;
+    e = launch_batch_kernel(b->d_reqs, items_b, b->nitems_b, b->d_next + 1, b->launch_b, b->aux);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaEventRecord(b->ev_join, b->aux)) != cudaSuccess) return e;
+    e = launch_batch_kernel(b->d_reqs, items_a, b->nitems_a, b->d_next, b->launch_a, s);
+    if (e != cudaSuccess) return e;
+    return cudaStreamWaitEvent(s, b->ev_join, 0);
+  }
+  if (b->nitems_a > 0)
+    return launch_batch_kernel(b->d_reqs, items_a, b->nitems_a, b->d_next, b->launch_a, s);
+  return launch_batch_kernel(b->d_reqs, items_b, b->nitems_b, b->d_next + 1, b->launch_b, s);
 }
 
 }  // namespace
@@ -383,7 +413,7 @@ mknn_status mknn_batch_create(const mknn_batch_req* reqs, int32_t nreq,
     }
     if (R.nq > 0 && (!R.q || !R.out_idx || !R.out_d2))
       return bfail(MKNN_EINVAL, "request " + std::to_string(r) + ": NULL device pointer");
-    const int lanes = o.lanes ? o.lanes : choose_lanes(R.k, R.cloud->n, plan_nq);
+    const int lanes = o.lanes ? o.lanes : choose_lanes(R.k, R.cloud->n, R.cloud->hub_bucket(), plan_nq);
     if (variant_index(lanes, R.k) < 0)
       return bfail(MKNN_EINVAL, "request " + std::to_string(r) + ": lanes/k combination");
     b->lanes[r] = lanes;
@@ -409,14 +439,18 @@ mknn_status mknn_batch_create(const mknn_batch_req* reqs, int32_t nreq,
   std::vector<int> orderq(nreq);
   for (int r = 0; r < nreq; ++r) orderq[r] = r;
   std::stable_sort(orderq.begin(), orderq.end(), [&](int a, int c) { return cost[a] > cost[c]; });
-  std::vector<Item> items;
-  for (int r : orderq) {
-    const int v = variant_index(b->lanes[r], reqs[r].k);
-    const int per = item_queries(b->lanes[r], rounds);
-    for (int64_t s0 = 0; s0 < reqs[r].nq; s0 += per)
-      items.push_back(Item{r, (int32_t)s0, (int32_t)std::min<int64_t>(reqs[r].nq, s0 + per), v});
+  std::vector<Item> items;       // family A (one lane, shared memory) first, then B
+  for (int fam = 0; fam < 2; ++fam) {
+    for (int r : orderq) {
+      if ((b->lanes[r] == 1) != (fam == 0)) continue;
+      const int v = variant_index(b->lanes[r], reqs[r].k);
+      const int per = item_queries(b->lanes[r], rounds);
+      for (int64_t s0 = 0; s0 < reqs[r].nq; s0 += per)
+        items.push_back(Item{r, (int32_t)s0, (int32_t)std::min<int64_t>(reqs[r].nq, s0 + per), v});
+    }
+    if (fam == 0) b->nitems_a = (int)items.size();
   }
-  b->nitems = (int)items.size();
+  b->nitems_b = (int)items.size() - b->nitems_a;
   cudaError_t e;
   if ((e = cudaMalloc((void**)&b->d_reqs, sizeof(ReqDev) * std::max(nreq, 1))) != cudaSuccess ||
       (e = cudaMalloc((void**)&b->d_items, sizeof(Item) * std::max<size_t>(items.size(), 1))) !=
@@ -439,14 +473,19 @@ mknn_status mknn_batch_create(const mknn_batch_req* reqs, int32_t nreq,
     return bfail(MKNN_ECUDA, std::string("plan upload: ") + cudaGetErrorString(e));
   }
   int kcap = 0;
-  bool smem_only = nreq > 0;
-  for (int r = 0; r < nreq; ++r) {
-    if (b->lanes[r] == 1)
-      kcap = std::max(kcap, (int)reqs[r].k);
-    else
-      smem_only = false;
+  for (int r = 0; r < nreq; ++r)
+    if (b->lanes[r] == 1) kcap = std::max(kcap, (int)reqs[r].k);
+  b->launch_a = batch_config(b->nitems_a, o.blocks_per_sm, kcap, true);
+  b->launch_b = batch_config(b->nitems_b, o.blocks_per_sm, 0, false);
+  if (b->nitems_a > 0 && b->nitems_b > 0) {
+    if ((e = cudaStreamCreateWithFlags(&b->aux, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming)) != cudaSuccess) {
+      mknn_batch* raw = b.release();
+      free_plan(raw);
+      return bfail(MKNN_ECUDA, std::string("plan streams: ") + cudaGetErrorString(e));
+    }
   }
-  b->launch = batch_config(b->nitems, o.blocks_per_sm, kcap, smem_only);
   if (o.graph >= 0) {
     cudaStream_t cs;
     if ((e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking)) == cudaSuccess) {
@@ -490,8 +529,9 @@ mknn_status mknn_batch_info(const mknn_batch* b, int32_t* lanes_out, int64_t* it
   if (!b) return bfail(MKNN_EINVAL, "plan is NULL");
   if (lanes_out)
     for (int r = 0; r < b->nreq; ++r) lanes_out[r] = b->lanes[r];
-  if (items) *items = b->nitems;
-  if (grid) *grid = b->launch.grid;
+  if (items) *items = (int64_t)b->nitems_a + b->nitems_b;
+  if (grid)
+    *grid = (b->nitems_a > 0 ? b->launch_a.grid : 0) + (b->nitems_b > 0 ? b->launch_b.grid : 0);
   return MKNN_OK;
 }
 
@@ -517,7 +557,7 @@ mknn_status mknn_knn_batch(const mknn_batch_req* reqs, int32_t nreq, const mknn_
 }
 
 // Times each candidate lane width on a sample of every distinct (k, size
-// bucket) among the requests and records the fastest in the tuning table.
+// bucket, hub bucket) among the requests and records the fastest in the tuning table.
 mknn_status mknn_batch_tune(const mknn_batch_req* reqs, int32_t nreq, int64_t sample,
                             mknn_stream_t stream) {
   if (nreq < 0 || (nreq > 0 && !reqs)) return bfail(MKNN_EINVAL, "bad request array");
@@ -540,7 +580,7 @@ mknn_status mknn_batch_tune(const mknn_batch_req* reqs, int32_t nreq, int64_t sa
   for (int r = 0; r < nreq && st == MKNN_OK; ++r) {
     const mknn_batch_req& R = reqs[r];
     if (!R.cloud || R.nq <= 0) continue;
-    const TuneKey key{R.k, nbucket_of(R.cloud->n)};
+    const TuneKey key{R.k, nbucket_of(R.cloud->n), R.cloud->hub_bucket()};
     if (seen.count(key)) continue;
     seen[key] = 1;
     const size_t need = (size_t)ns * R.k * 4;
@@ -590,12 +630,19 @@ mknn_status mknn_batch_tune(const mknn_batch_req* reqs, int32_t nreq, int64_t sa
         if (rep > 0) ms_min = std::min(ms_min, ms);
       }
       if (st != MKNN_OK) break;
+      if (const char* logp = std::getenv("MKNN_TUNE_LOG")) {
+        if (FILE* lf = std::fopen(logp, "a")) {
+          std::fprintf(lf, "k=%d n=%lld hub=%d sample=%lld lanes=%d ms=%.4f\n", R.k,
+                       (long long)R.cloud->n, key.hub, (long long)ns, lanes, ms_min);
+          std::fclose(lf);
+        }
+      }
       if (ms_min < best_ms) {
         best_ms = ms_min;
         best = lanes;
       }
     }
-    if (st == MKNN_OK && best) set_tuned_lanes(R.k, R.cloud->n, best);
+    if (st == MKNN_OK && best) set_tuned_lanes(R.k, R.cloud->n, key.hub, best);
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -611,8 +658,9 @@ mknn_status mknn_tune_save(const char* path) {
   FILE* f = std::fopen(path, "w");
   if (!f) return bfail(MKNN_EIO, std::string("cannot open ") + path);
   std::lock_guard<std::mutex> lk(g_tune_mu);
-  std::fprintf(f, "# k log2(n) lanes\n");
-  for (auto& kv : g_tune) std::fprintf(f, "%d %d %d\n", kv.first.k, kv.first.nbucket, kv.second);
+  std::fprintf(f, "# k log2(n) log2(1+longest list) lanes\n");
+  for (auto& kv : g_tune)
+    std::fprintf(f, "%d %d %d %d\n", kv.first.k, kv.first.nbucket, kv.first.hub, kv.second);
   return std::fclose(f) == 0 ? MKNN_OK : bfail(MKNN_EIO, "write failed");
 }
 
@@ -624,9 +672,10 @@ mknn_status mknn_tune_load(const char* path) {
   std::map<TuneKey, int> t;
   while (std::fgets(line, sizeof line, f)) {
     if (line[0] == '#') continue;
-    int k, nb, lanes;
-    if (std::sscanf(line, "%d %d %d", &k, &nb, &lanes) == 3 && variant_index(lanes, k) >= 0)
-      t[TuneKey{k, nb}] = lanes;
+    int k, nb, hub, lanes;
+    if (std::sscanf(line, "%d %d %d %d", &k, &nb, &hub, &lanes) == 4 &&
+        variant_index(lanes, k) >= 0)
+      t[TuneKey{k, nb, hub}] = lanes;
   }
   std::fclose(f);
   std::lock_guard<std::mutex> lk(g_tune_mu);

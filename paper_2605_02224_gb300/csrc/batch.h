@@ -49,13 +49,15 @@ cudaError_t launch_batch_kernel(const ReqDev* d_reqs, const Item* d_items, int n
                                 const BatchLaunch& b, cudaStream_t s);
 
 // Lanes per query recorded by the tuner for (k, floor(log2 n)), 0 if none.
-int tuned_lanes(int k, int64_t n);
-void set_tuned_lanes(int k, int64_t n, int lanes);
+// The tuning table is keyed by k, floor(log2 n) and the cloud's hub bucket
+// (floor(log2(1 + longest successor list))).
+int tuned_lanes(int k, int64_t n, int hub);
+void set_tuned_lanes(int k, int64_t n, int hub, int lanes);
 // Lanes per query for a launch of nq queries: the tuned (or default) value
-// for (k, n), widened for batches too small to fill the GPU one query per
-// thread.
-int choose_lanes(int k, int64_t n, int64_t nq);
-// The smallest lane width that fills the GPU with nq queries.
-int fill_lanes(int64_t nq);
+// for (k, n, hub), widened for batches too small to fill the GPU one query
+// per thread.
+int choose_lanes(int k, int64_t n, int hub, int64_t nq);
+// The smallest lane width that fills the GPU with nq queries of this k.
+int fill_lanes(int64_t nq, int k);
 
 }  // namespace mknn

@@ -454,7 +454,7 @@ mknn_status mknn_knn_ex(const mknn_cloud* c, const float* q, int64_t nq, int32_t
   }
   if (nq == 0) return MKNN_OK;
   if (!q || !out_idx || !out_d2) return fail(MKNN_EINVAL, "NULL device pointer");
-  int lanes = (opts && opts->lanes) ? opts->lanes : choose_lanes(k, c->n, nq);
+  int lanes = (opts && opts->lanes) ? opts->lanes : choose_lanes(k, c->n, c->hub_bucket(), nq);
   if (lanes != 1 && lanes != 4 && lanes != 8 && lanes != 16 && lanes != 32)
     return fail(MKNN_EINVAL, "lanes must be 1, 4, 8, 16 or 32");
   cudaStream_t s = (cudaStream_t)stream;

@@ -1,5 +1,6 @@
 // The cloud object behind the opaque mknn_cloud handle (internal).
 #pragma once
+#include <algorithm>
 #include <atomic>
 #include <cstdint>
 #include <mutex>
@@ -29,6 +30,19 @@ struct mknn_cloud {
   mutable std::mutex mu;
 
   int64_t E() const { return (int64_t)succ.size(); }
+  // floor(log2(1 + longest successor list)): the tuning table's cloud shape
+  // key (hub rows make queries costly whatever the size)
+  int hub_bucket() const {
+    int hb = hub_.load(std::memory_order_relaxed);
+    if (hb >= 0) return hb;
+    int64_t mx = 0;
+    for (size_t i = 0; i + 1 < rowp.size(); ++i) mx = std::max<int64_t>(mx, rowp[i + 1] - rowp[i]);
+    hb = 0;
+    while ((int64_t(2) << hb) <= mx + 1) ++hb;
+    hub_.store(hb, std::memory_order_relaxed);
+    return hb;
+  }
+  mutable std::atomic<int> hub_{-1};
   mknn::CloudDevHost dev() const {
     mknn::CloudDevHost c;
     c.pts = d_pts;

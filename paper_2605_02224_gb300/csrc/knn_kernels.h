@@ -27,7 +27,7 @@ struct PlainLaunch {
   int32_t* err;          // device error word
   int lanes;             // 1, 4, 8, 16, 32
   int blocks_per_sm;     // 0 = occupancy limit
-  int placement = 1;     // lanes == 1: 1 = registers per thread, 2 = shared-memory warp tile
+  int placement = 1;     // lanes == 1: 1 = registers per thread, 2 = shared-memory lists
 };
 
 // Launches the plain (one cloud) query kernel. Returns a CUDA error code.

@@ -119,6 +119,9 @@ __global__ void __launch_bounds__(THREADS) knn_plain_smem_kernel(
   float* dcol = reinterpret_cast<float*>(wbase) + lane;
   uint32_t* rcol = wbase + kcap * 32 + lane;
   const int64_t stride = (int64_t)gridDim.x * THREADS;
+  // Each thread moves on to its next query as soon as it is done with one:
+  // nothing makes the warp's lanes wait for each other at query boundaries
+  // (a warp-synchronous variant that did was measured 1.3x-1.6x slower).
   for (int64_t i = (int64_t)blockIdx.x * THREADS + threadIdx.x; i < nq; i += stride) {
     const int64_t qi = perm ? (int64_t)__ldg(perm + i) : i;
     const float* qp = q + qi * q_stride;

@@ -104,6 +104,8 @@ struct ReqRec {
 
 struct Slot {
   cudaStream_t s = nullptr;
+  cudaStream_t aux = nullptr;    // second branch for packs with both kernel families
+  cudaEvent_t fork = nullptr, join = nullptr;
   cudaEvent_t done = nullptr;
   bool busy = false;
   std::vector<uint64_t> tickets;
@@ -228,10 +230,9 @@ void mknn_server::launch(Slot& sl, std::vector<uint64_t>& tickets, size_t off, s
     const size_t reqs_off = 256 + kSortHistBytes;
     const int nreq = (int)tickets.size();
     std::vector<ReqDev> rd(nreq);
-    std::vector<Item> items;
+    std::vector<Item> items_a, items_b;  // one-lane requests | group requests
     int kcap = 0;
-    bool smem_only = true;
-    int64_t pack_nq = 0;  // the pack runs in one launch: its size sets the lane width
+    int64_t pack_nq = 0;  // the pack runs as one launch per family: its size sets the lanes
     for (int i = 0; i < nreq; ++i) pack_nq += recs[tickets[i] - 1].r.nq;
     for (int i = 0; i < nreq; ++i) {
       ReqRec& R = recs[tickets[i] - 1];
@@ -250,7 +251,7 @@ void mknn_server::launch(Slot& sl, std::vector<uint64_t>& tickets, size_t off, s
         e = launch_query_sort_split(cd, (const float*)(dbase + R.q_off), 3, q.nq, d_hist,
                                     (int32_t*)(dbase + R.cell_off), (int32_t*)(dbase + R.perm_off),
                                     s);
-      const int lanes = o.lanes ? o.lanes : choose_lanes(q.k, c->n, pack_nq);
+      const int lanes = o.lanes ? o.lanes : choose_lanes(q.k, c->n, c->hub_bucket(), pack_nq);
       rd[i] = ReqDev{(const float4*)cd.pts, cd.rowp, cd.succ, cd.n, 3,
                      (const float*)(dbase + R.q_off), nullptr,
                      sorted ? (const int32_t*)(dbase + R.perm_off) : nullptr,
@@ -258,26 +259,41 @@ void mknn_server::launch(Slot& sl, std::vector<uint64_t>& tickets, size_t off, s
                      q.m ? q.m : (int32_t)c->n};
       const int v = variant_index(lanes, q.k);
       const int per = item_queries(lanes, 8);
-      if (lanes == 1)
-        kcap = std::max(kcap, (int)q.k);
-      else
-        smem_only = false;
+      if (lanes == 1) kcap = std::max(kcap, (int)q.k);
+      std::vector<Item>& dst = lanes == 1 ? items_a : items_b;
       for (int64_t b0 = 0; b0 < q.nq; b0 += per)
-        items.push_back(Item{i, (int32_t)b0, (int32_t)std::min<int64_t>(q.nq, b0 + per), v});
+        dst.push_back(Item{i, (int32_t)b0, (int32_t)std::min<int64_t>(q.nq, b0 + per), v});
     }
+    const int na = (int)items_a.size(), nb = (int)items_b.size();
     const size_t items_off = reqs_off + al(sizeof(ReqDev) * nreq);
     // request table and items go through the pinned mirror
     std::memcpy(hbase + reqs_off, rd.data(), sizeof(ReqDev) * nreq);
-    std::memcpy(hbase + items_off, items.data(), sizeof(Item) * items.size());
+    std::memcpy(hbase + items_off, items_a.data(), sizeof(Item) * na);
+    std::memcpy(hbase + items_off + sizeof(Item) * na, items_b.data(), sizeof(Item) * nb);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(dbase + reqs_off, hbase + reqs_off,
-                          items_off - reqs_off + sizeof(Item) * items.size(),
+                          items_off - reqs_off + sizeof(Item) * (na + nb),
                           cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(d_next, 0, sizeof(int), s);
-    if (e == cudaSuccess)
-      e = launch_batch_kernel((const ReqDev*)(dbase + reqs_off), (const Item*)(dbase + items_off),
-                              (int)items.size(), d_next,
-                              batch_config((int)items.size(), 0, kcap, smem_only), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_next, 0, 2 * sizeof(int), s);
+    const ReqDev* d_reqs = (const ReqDev*)(dbase + reqs_off);
+    const Item* d_items = (const Item*)(dbase + items_off);
+    if (e == cudaSuccess && na > 0 && nb > 0) {
+      // both families: the group kernel runs on the slot's second stream,
+      // concurrently with the one-lane kernel, and joins before the copies
+      e = cudaEventRecord(sl.fork, s);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(sl.aux, sl.fork, 0);
+      if (e == cudaSuccess)
+        e = launch_batch_kernel(d_reqs, d_items + na, nb, d_next + 1,
+                                batch_config(nb, 0, 0, false), sl.aux);
+      if (e == cudaSuccess) e = cudaEventRecord(sl.join, sl.aux);
+      if (e == cudaSuccess)
+        e = launch_batch_kernel(d_reqs, d_items, na, d_next, batch_config(na, 0, kcap, true), s);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(s, sl.join, 0);
+    } else if (e == cudaSuccess && na > 0) {
+      e = launch_batch_kernel(d_reqs, d_items, na, d_next, batch_config(na, 0, kcap, true), s);
+    } else if (e == cudaSuccess) {
+      e = launch_batch_kernel(d_reqs, d_items, nb, d_next + 1, batch_config(nb, 0, 0, false), s);
+    }
     for (int i = 0; i < nreq && e == cudaSuccess; ++i) {
       ReqRec& R = recs[tickets[i] - 1];
       const size_t nk = (size_t)R.r.nq * R.r.k * 4;
@@ -408,6 +424,9 @@ mknn_status mknn_server_create(const mknn_server_opts* opts, mknn_server** out) 
   s->slots.resize(s->o.slots);
   for (Slot& sl : s->slots) {
     if (cudaStreamCreateWithFlags(&sl.s, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&sl.aux, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&sl.fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&sl.join, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess) {
       cudaGetLastError();
       return sfail(MKNN_ECUDA, "stream/event creation failed");
@@ -556,8 +575,12 @@ mknn_status mknn_server_destroy(mknn_server* s, double timeout_s) {
   s->th.join();
   for (Slot& sl : s->slots) {
     cudaStreamSynchronize(sl.s);
+    cudaStreamSynchronize(sl.aux);
     cudaEventDestroy(sl.done);
+    cudaEventDestroy(sl.fork);
+    cudaEventDestroy(sl.join);
     cudaStreamDestroy(sl.s);
+    cudaStreamDestroy(sl.aux);
   }
   for (mknn_cloud* c : s->clouds) c->holders--;
   cudaFree(s->d_arena);

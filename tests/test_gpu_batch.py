@@ -125,10 +125,12 @@ def test_tuner_fills_table_and_plan_uses_it(torch, clouds, tmp_path):
     M.mknn_tune_load(path)
     plan = M.mknn_batch_create(reqs)
     lanes, _, _ = M.mknn_batch_info(plan, len(reqs))
-    table = {(int(a), int(b)): int(c) for a, b, c in (l.split() for l in lines)}
-    for (wl, *_), l in zip(keep, lanes):
-        key = (wl.k, int(np.floor(np.log2(wl.n))))
-        assert table.get(key, l) == l
+    table = {(int(a), int(b), int(h)): int(c) for a, b, h, c in (l.split() for l in lines)}
+    for (wl, c, *_), l in zip(keep, lanes):
+        longest = int(np.diff(c.table()[1]).max())
+        key = (wl.k, int(np.floor(np.log2(wl.n))), int(np.floor(np.log2(1 + longest))))
+        assert key in table
+        assert table[key] == l or l > table[key]   # widened only to fill the GPU
     M.mknn_batch_run(plan, s)
     torch.cuda.synchronize()
     for wl, c, q, m, ms, idx, d2 in keep:

@@ -15,8 +15,11 @@ from tests.gpu_util import built_cloud, run_knn
 pytestmark = pytest.mark.gpu
 
 LANES = (1, 4, 8, 16, 32)
-# (lanes per query, candidate-list placement): 1 = registers, 2 = shared-memory warp tile
-VARIANTS = ((1, 1), (1, 2), (4, 1), (8, 1), (16, 1), (32, 1))
+# lanes per query; one-lane candidate-list placement (1 = registers, 2 = shared
+# memory)
+VARIANTS = (dict(lanes=1, placement=1), dict(lanes=1, placement=2),
+            dict(lanes=4, placement=1), dict(lanes=8, placement=1), dict(lanes=16, placement=1),
+            dict(lanes=32, placement=1))
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -43,10 +46,10 @@ def test_tiny_exhaustive(n, table):
     Q = W.box_queries(60, 7, [-1.5] * 3, [1.5] * 3)
     Q = np.concatenate([Q, Pr[: min(n, 20)]])          # queries exactly on sites
     ks = sorted({1, 2, min(n, 8), min(n + 1, 64), 33, 64})
-    for lanes, pl in VARIANTS:
+    for v in VARIANTS:
         for k in ks:
             for m in sorted({1, max(1, n // 2), n}):
-                idx, d2 = run_knn(c, Q, k, m, lanes=lanes, placement=pl, sort=1 if k % 2 else -1)
+                idx, d2 = run_knn(c, Q, k, m, **v, sort=1 if k % 2 else -1)
                 parity.check_rows(Pr, Q, k, m, idx, d2)
     c.close()
 
@@ -56,8 +59,8 @@ def test_small_sphere_workload_all_queries():
     wl = W.small_sphere()
     c = Cloud.build(wl.points, wl.order).upload()
     Pr = wl.ranked_points()
-    for lanes, pl in VARIANTS:
-        idx, d2 = run_knn(c, wl.queries, wl.k, lanes=lanes, placement=pl)
+    for v in VARIANTS:
+        idx, d2 = run_knn(c, wl.queries, wl.k, **v)
         parity.check_rows(Pr, wl.queries, wl.k, 0, idx, d2)
     idx0, d20 = run_knn(c, wl.queries, wl.k)
     assert c.check() == 0
@@ -70,8 +73,8 @@ def test_sphere_centre_closed_form():
     wl = W.small_sphere(nq=1)
     c = Cloud.build(wl.points, wl.order).upload()
     Q = np.zeros((4, 3), np.float32)
-    for lanes, pl in VARIANTS:
-        idx, d2 = run_knn(c, Q, 64, lanes=lanes, placement=pl)
+    for v in VARIANTS:
+        idx, d2 = run_knn(c, Q, 64, **v)
         assert np.all(np.abs(d2 - 1.0) <= 1e-6)
         assert all(np.unique(r).size == 64 for r in idx)
         assert np.all(idx >= 0) and np.all(idx < 2000)
@@ -92,8 +95,8 @@ def test_lattice_rings_closed_form():
     rng = np.random.default_rng(0)
     centres = rng.integers(5, L - 5, size=(50, 3)).astype(np.float32)
     for k in (1, 7, 19, 27, 33):
-        for lanes, pl in VARIANTS:
-            idx, d2 = run_knn(c, centres, k, lanes=lanes, placement=pl)
+        for v in VARIANTS:
+            idx, d2 = run_knn(c, centres, k, **v)
             parity.check_rows(P, centres, k, 0, idx, d2)
             cum = np.cumsum([r3[s] for s in range(13)])
             smax = int(np.searchsorted(cum, k))
@@ -116,11 +119,43 @@ def test_prefix_bound_per_query_and_padding():
     m = np.clip(m, 1, 20000)
     m[:50] = np.arange(1, 51)                       # m < k: padded rows
     for k in (1, 10, 64):
-        for lanes, pl in VARIANTS:
-            idx, d2 = run_knn(c, Q, k, m, lanes=lanes, placement=pl)
+        for v in VARIANTS:
+            idx, d2 = run_knn(c, Q, k, m, **v)
             parity.check_row_properties(idx, d2, k, m.astype(np.int64), 20000)
             parity.check_rows(Pr, Q, k, m, idx, d2, rows=range(0, nq, 7))
     assert c.check() == 0
+    c.close()
+
+
+def test_hub_rows_all_variants():
+    """Four nearly planar patches: a few successor lists hold hundreds to
+    thousands of entries (hubs). Every row against the oracle, per-query m
+    included, for every kernel variant; all variants give the same bits."""
+    P, _ = W.patches4(30000, 61)
+    order = W.permutation(30000, 62)
+    c = built_cloud(P, order, "patches30k")
+    c.upload()
+    Pr = P[order]
+    _, rowp, _ = c.table()
+    assert np.diff(rowp).max() > 500                   # the workload has hubs
+    nq = 1500
+    Q = np.concatenate([W.box_queries(nq // 3, 63, [0.0] * 3, [1.0] * 3),
+                        Pr[W.permutation(30000, 64)[: nq // 3]]
+                        + 1e-3 * W.normal(65, 1, nq // 3 * 3).reshape(-1, 3).astype(np.float32),
+                        Pr[: nq - 2 * (nq // 3)]]).astype(np.float32)
+    m = np.clip(np.floor(np.exp(W.uniform(66, 1, nq) * np.log(30000))), 1, 30000).astype(np.int32)
+    for k in (1, 8, 33, 64):
+        mk = m if k != 8 else None
+        base = None
+        for v in VARIANTS:
+            if v["lanes"] == 4 and k > 16:
+                continue
+            idx, d2 = run_knn(c, Q, k, mk, **v)
+            if base is None:
+                parity.check_rows(Pr, Q, k, mk if mk is not None else 0, idx, d2)
+                base = (idx, d2)
+            else:
+                assert np.array_equal(idx, base[0]) and np.array_equal(d2, base[1]), (k, v)
     c.close()
 
 
@@ -156,8 +191,8 @@ def test_duplicates_and_degenerate_clouds():
     Pr = P[order]
     Q = np.concatenate([W.box_queries(500, 78, [-1] * 3, [8] * 3), Pr[:100]]).astype(np.float32)
     for k in (1, 2, 9, 27, 64):
-        for lanes, pl in ((1, 1), (1, 2), (8, 1), (32, 1)):
-            idx, d2 = run_knn(c, Q, k, lanes=lanes, placement=pl)
+        for v in VARIANTS:
+            idx, d2 = run_knn(c, Q, k, **v)
             parity.check_rows(Pr, Q, k, 0, idx, d2)
     c.close()
 
@@ -229,8 +264,8 @@ def test_large_torus_full_size_sampled():
     c.upload()
     idx, d2 = run_knn(c, wl.queries, wl.k)
     parity.check_row_properties(idx, d2, wl.k, np.full(wl.nq, wl.n, np.int64), wl.n)
-    for lanes, pl in ((1, 2), (16, 1)):              # other variants give the same rows
-        i2, d22 = run_knn(c, wl.queries, wl.k, lanes=lanes, placement=pl)
+    for v in (dict(lanes=1, placement=1), dict(lanes=16, placement=1)):
+        i2, d22 = run_knn(c, wl.queries, wl.k, **v)      # other variants: the same rows
         assert np.array_equal(i2, idx) and np.array_equal(d22, d2)
     Pr = wl.ranked_points()
     rows = np.linspace(0, wl.nq - 1, 400).astype(np.int64)
