@@ -277,7 +277,9 @@ mknn_status mknn_batch_create(const mknn_batch_req* reqs, int32_t nreq,
 /* Enqueues one run of the plan on the stream (asynchronous). Runs of one
  * plan must not overlap on the device (they share the queue counter). */
 mknn_status mknn_batch_run(mknn_batch* plan, mknn_stream_t stream);
-/* Lanes chosen per request (int32[nreq], may be NULL), work items, grid. */
+/* Lanes chosen per request (int32[nreq], may be NULL), work items, and the
+ * blocks of the plan's persistent launches (one launch per kernel variant
+ * present, summed). */
 mknn_status mknn_batch_info(const mknn_batch* plan, int32_t* lanes, int64_t* items, int32_t* grid);
 mknn_status mknn_batch_free(mknn_batch* plan);
 /* One-shot: create (without a graph), run, synchronise the stream, free. */
@@ -299,9 +301,11 @@ mknn_status mknn_knn_batch(const mknn_batch_req* reqs, int32_t nreq, const mknn_
  * Synchronises the stream. Errors: EINVAL, ENOMEM, ECUDA. */
 mknn_status mknn_batch_tune(const mknn_batch_req* reqs, int32_t nreq, int64_t sample,
                             mknn_stream_t stream);
-/* Tuning table as text ("k log2n hub lanes" per line). */
+/* Tuning table as text ("k log2n hub lanes" per line); load merges into
+ * the table, clear empties it (the untuned defaults apply again). */
 mknn_status mknn_tune_save(const char* path);
 mknn_status mknn_tune_load(const char* path);
+mknn_status mknn_tune_clear(void);
 
 /* ---------------------------------------------------------------- serving
  * A request loop over resident clouds with continuous batching: a

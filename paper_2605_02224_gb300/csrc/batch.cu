@@ -3,14 +3,15 @@
 // plan.
 //
 // A plan covers many requests, each (cloud, queries, k, m, outputs). Every
-// request is cut into work items of a few rounds of its group width; one
-// persistent launch (SM count x resident blocks) drains the item queue:
-// each warp takes the next item with one atomic and serves it with the
-// variant (lanes per query G, candidate slots per lane S) the tuner chose
-// for that request's (k, cloud size). Items of one request are contiguous
-// in the queue, so the warps working at any moment share one cloud's table
-// in L2; requests are queued by decreasing estimated cost so that the
-// queue ends with short items.
+// request is served by the kernel variant (lanes per query G, candidate
+// slots per lane S) the tuner chose for its (k, cloud size, cloud shape),
+// and cut into work items of a few rounds of its group width. The items of
+// each variant form one queue, drained by one persistent launch of that
+// variant's kernel (SM count x resident blocks): each warp takes the next
+// item with one atomic. Items of one request are contiguous in a queue, so
+// the warps working at any moment share one cloud's table in L2; requests
+// are queued by decreasing estimated cost so that a queue ends with short
+// items. The one-lane launch and the group launches run on two streams.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -46,7 +47,7 @@ constexpr VariantDesc kVariants[] = {{4, 1},  {4, 2},  {4, 4},  {8, 1},  {8, 2},
                                      {8, 4},  {8, 8},  {16, 1}, {16, 2}, {16, 4},
                                      {32, 1}, {32, 2}, {1, 64}};
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
-constexpr int kSmemVariant = 12;
+static_assert(kVariants[kSmemVariant].g == 1, "one-lane variant index");
 
 }  // namespace
 
@@ -62,16 +63,13 @@ int variant_index(int g, int k) {
 namespace {
 
 // This thread's column of its warp's shared-memory candidate lists.
-__device__ __forceinline__ void smem_columns(int kcap, float** dcol, uint32_t** rcol) {
-  extern __shared__ uint32_t batch_lists[];
+__device__ __forceinline__ uint64_t* smem_column(int kcap) {
+  extern __shared__ uint64_t batch_lists[];
   const int warp = (int)(threadIdx.x >> 5), lane = (int)(threadIdx.x & 31u);
-  uint32_t* wbase = batch_lists + (size_t)warp * 2 * kcap * 32;
-  *dcol = reinterpret_cast<float*>(wbase) + lane;
-  *rcol = wbase + kcap * 32 + lane;
+  return batch_lists + (size_t)warp * kcap * 32 + lane;
 }
 
-__device__ __forceinline__ void serve_item_smem(const ReqDev& R, const Item& w, float* dcol,
-                                                uint32_t* rcol) {
+__device__ __forceinline__ void serve_item_smem(const ReqDev& R, const Item& w, uint64_t* col) {
   const int lane = (int)(threadIdx.x & 31u);
   const CloudDev C{R.pts, R.rowp, R.succ, R.n};
   for (int i = w.begin + lane; i < w.end; i += 32) {
@@ -89,7 +87,7 @@ __device__ __forceinline__ void serve_item_smem(const ReqDev& R, const Item& w, 
       atomicOr(R.err, 1);
       continue;
     }
-    knn_query_smem(C, qx, qy, qz, R.k, m, dcol, rcol, oi, od);
+    knn_query_smem(C, qx, qy, qz, R.k, m, col, oi, od);
   }
 }
 
@@ -116,65 +114,50 @@ __device__ __forceinline__ void serve_item(const ReqDev& R, const Item& w) {
   }
 }
 
-// The group variants (lists in registers). Three resident blocks per SM
-// caps the variants' union at 80 registers (a few bytes of spill in the
-// largest) instead of 118.
-__global__ void __launch_bounds__(kThreads, 3) knn_batch_kernel(const ReqDev* __restrict__ reqs,
-                                                             const Item* __restrict__ items,
-                                                             int nitems, int* __restrict__ next,
-                                                             int kcap) {
+// One group variant (lists in registers) per kernel, so that each gets the
+// registers it needs and the occupancy that follows (a single kernel holding
+// every variant behind a switch was held to the largest one's registers).
+template <int G, int S>
+__global__ void __launch_bounds__(kThreads) knn_batch_group_kernel(const ReqDev* __restrict__ reqs,
+                                                                   const Item* __restrict__ items,
+                                                                   int nitems,
+                                                                   int* __restrict__ next,
+                                                                   int kcap) {
+  (void)kcap;  // lists in registers
   const uint32_t lane = threadIdx.x & 31u;
-  (void)kcap;  // the group variants keep their lists in registers
   for (;;) {
     int it = 0;
     if (lane == 0) it = atomicAdd(next, 1);
     it = __shfl_sync(0xffffffffu, it, 0);
     if (it >= nitems) return;
     const Item w = items[it];
-    const ReqDev R = reqs[w.req];
-    switch (w.variant) {
-      case 0: serve_item<4, 1>(R, w); break;
-      case 1: serve_item<4, 2>(R, w); break;
-      case 2: serve_item<4, 4>(R, w); break;
-      case 3: serve_item<8, 1>(R, w); break;
-      case 4: serve_item<8, 2>(R, w); break;
-      case 5: serve_item<8, 4>(R, w); break;
-      case 6: serve_item<8, 8>(R, w); break;
-      case 7: serve_item<16, 1>(R, w); break;
-      case 8: serve_item<16, 2>(R, w); break;
-      case 9: serve_item<16, 4>(R, w); break;
-      case 10: serve_item<32, 1>(R, w); break;
-      case 11: serve_item<32, 2>(R, w); break;
-      default: break;  // one-lane items go to knn_batch_smem_kernel
-    }
+    serve_item<G, S>(reqs[w.req], w);
     __syncwarp();
   }
 }
 
-// The shared-memory one-query-per-thread variant alone (48 registers):
-// used when every request of a launch takes it, the default.
+// The one-lane variant: one query per thread, candidate lists in shared
+// memory, 256-thread blocks held to 48 registers as in the plain kernel.
 template <int THREADS>
-__global__ void __launch_bounds__(THREADS) knn_batch_smem_kernel(const ReqDev* __restrict__ reqs,
+__global__ void __launch_bounds__(THREADS, THREADS == 256 ? 5 : 1) knn_batch_smem_kernel(const ReqDev* __restrict__ reqs,
                                                                  const Item* __restrict__ items,
                                                                  int nitems,
                                                                  int* __restrict__ next,
                                                                  int kcap) {
   const uint32_t lane = threadIdx.x & 31u;
-  float* dcol;
-  uint32_t* rcol;
-  smem_columns(kcap, &dcol, &rcol);
+  uint64_t* col = smem_column(kcap);
   for (;;) {
     int it = 0;
     if (lane == 0) it = atomicAdd(next, 1);
     it = __shfl_sync(0xffffffffu, it, 0);
     if (it >= nitems) return;
     const Item w = items[it];
-    serve_item_smem(reqs[w.req], w, dcol, rcol);
+    serve_item_smem(reqs[w.req], w, col);
     __syncwarp();
   }
 }
 
-size_t list_bytes(int threads, int kcap) { return (size_t)threads * 2 * (size_t)kcap * 4; }
+size_t list_bytes(int threads, int kcap) { return (size_t)threads * (size_t)kcap * 8; }
 
 inline size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
@@ -197,7 +180,13 @@ int nbucket_of(int64_t n) {
   return b;
 }
 
-int heuristic_lanes(int k) { return default_lanes(k); }
+// Untuned default: one query per thread, except on clouds with hub rows
+// (a successor list of 2^12 entries or more, typical of nearly coplanar
+// sites), where a whole warp per query scans the long rows 32 entries at a
+// time. Timed on 64 mixed clouds, 32 lanes won on 16 of the 17 hub clouds
+// (by 1.2x-3.9x) and lost on all but one of the others (by up to 20x).
+constexpr int kHubBucketWide = 12;
+int heuristic_lanes(int k, int hub) { return hub >= kHubBucketWide ? 32 : default_lanes(k); }
 
 }  // namespace
 
@@ -216,7 +205,7 @@ int fill_lanes(int64_t nq, int k) {
 
 int choose_lanes(int k, int64_t n, int hub, int64_t nq) {
   const int t = tuned_lanes(k, n, hub);
-  int lanes = std::max(t ? t : heuristic_lanes(k), fill_lanes(nq, k));
+  int lanes = std::max(t ? t : heuristic_lanes(k, hub), fill_lanes(nq, k));
   while (lanes < 32 && variant_index(lanes, k) < 0) lanes <<= 1;  // e.g. 4 lanes hold k <= 16
   return lanes;
 }
@@ -228,12 +217,9 @@ std::once_flag g_attr_once;
 cudaError_t g_attr_err = cudaSuccess;
 
 void set_smem_attributes() {
-  cudaError_t e = cudaFuncSetAttribute(knn_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)list_bytes(kThreads, 64));
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(knn_batch_smem_kernel<256>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)list_bytes(256, 32));
+  cudaError_t e = cudaFuncSetAttribute(knn_batch_smem_kernel<256>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)list_bytes(256, 32));
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(knn_batch_smem_kernel<128>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -241,24 +227,45 @@ void set_smem_attributes() {
   g_attr_err = e;
 }
 
+// The kernel of a variant (the one-lane kernel by its block size).
+const void* variant_kernel(int variant, int threads) {
+  switch (variant) {
+    case 0: return (const void*)knn_batch_group_kernel<4, 1>;
+    case 1: return (const void*)knn_batch_group_kernel<4, 2>;
+    case 2: return (const void*)knn_batch_group_kernel<4, 4>;
+    case 3: return (const void*)knn_batch_group_kernel<8, 1>;
+    case 4: return (const void*)knn_batch_group_kernel<8, 2>;
+    case 5: return (const void*)knn_batch_group_kernel<8, 4>;
+    case 6: return (const void*)knn_batch_group_kernel<8, 8>;
+    case 7: return (const void*)knn_batch_group_kernel<16, 1>;
+    case 8: return (const void*)knn_batch_group_kernel<16, 2>;
+    case 9: return (const void*)knn_batch_group_kernel<16, 4>;
+    case 10: return (const void*)knn_batch_group_kernel<32, 1>;
+    case 11: return (const void*)knn_batch_group_kernel<32, 2>;
+    case kSmemVariant:
+      return threads == 256 ? (const void*)knn_batch_smem_kernel<256>
+                            : (const void*)knn_batch_smem_kernel<128>;
+    default: return nullptr;
+  }
+}
+
 }  // namespace
 
-BatchLaunch batch_config(int nitems, int blocks_per_sm, int kcap, bool smem_only) {
+BatchLaunch batch_config(int nitems, int blocks_per_sm, int kcap, int variant) {
   std::call_once(g_attr_once, set_smem_attributes);
   BatchLaunch b;
-  b.kcap = kcap;
-  b.smem_only = smem_only;
-  b.threads = smem_only ? (kcap <= 32 ? 256 : 128) : kThreads;
-  b.smem = kcap > 0 ? list_bytes(b.threads, kcap) : 0;
+  b.variant = variant;
+  const bool smem = variant == kSmemVariant;
+  b.kcap = smem ? kcap : 0;
+  b.threads = smem ? (kcap <= 32 ? 256 : 128) : kThreads;
+  b.smem = smem ? list_bytes(b.threads, kcap) : 0;
   int occ = 1;
-  cudaError_t e;
-  if (!smem_only)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, knn_batch_kernel, b.threads, b.smem);
-  else if (b.threads == 256)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, knn_batch_smem_kernel<256>, 256, b.smem);
-  else
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, knn_batch_smem_kernel<128>, 128, b.smem);
-  if (e != cudaSuccess || occ < 1) occ = 1;
+  const void* fn = variant_kernel(variant, b.threads);
+  if (!fn || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, b.threads, b.smem) !=
+                 cudaSuccess || occ < 1) {
+    cudaGetLastError();
+    occ = 1;
+  }
   const int per_sm = blocks_per_sm > 0 ? std::min(blocks_per_sm, occ) : occ;
   const int wpb = b.threads / 32;
   const int64_t blocks_needed = ((int64_t)std::max(1, nitems) + wpb - 1) / wpb;
@@ -270,13 +277,48 @@ cudaError_t launch_batch_kernel(const ReqDev* d_reqs, const Item* d_items, int n
                                 const BatchLaunch& b, cudaStream_t s) {
   if (nitems <= 0) return cudaSuccess;
   if (g_attr_err != cudaSuccess) return g_attr_err;
-  if (!b.smem_only)
-    knn_batch_kernel<<<b.grid, b.threads, b.smem, s>>>(d_reqs, d_items, nitems, d_next, b.kcap);
-  else if (b.threads == 256)
-    knn_batch_smem_kernel<256><<<b.grid, 256, b.smem, s>>>(d_reqs, d_items, nitems, d_next, b.kcap);
-  else
-    knn_batch_smem_kernel<128><<<b.grid, 128, b.smem, s>>>(d_reqs, d_items, nitems, d_next, b.kcap);
-  return cudaGetLastError();
+  const void* fn = variant_kernel(b.variant, b.threads);
+  if (!fn) return cudaErrorInvalidValue;
+  int kcap = b.kcap;
+  void* args[] = {(void*)&d_reqs, (void*)&d_items, (void*)&nitems, (void*)&d_next, (void*)&kcap};
+  return cudaLaunchKernel(fn, dim3((unsigned)b.grid), dim3((unsigned)b.threads), args, b.smem, s);
+}
+
+std::vector<Segment> make_segments(std::vector<Item>& items, int blocks_per_sm, int kcap) {
+  auto rank = [](int v) { return v == kSmemVariant ? -1 : v; };
+  std::stable_sort(items.begin(), items.end(),
+                   [&](const Item& a, const Item& c) { return rank(a.variant) < rank(c.variant); });
+  std::vector<Segment> segs;
+  for (int i = 0; i < (int)items.size();) {
+    int j = i;
+    while (j < (int)items.size() && items[j].variant == items[i].variant) ++j;
+    Segment g;
+    g.begin = i;
+    g.count = j - i;
+    g.launch = batch_config(g.count, blocks_per_sm, kcap, items[i].variant);
+    segs.push_back(g);
+    i = j;
+  }
+  return segs;
+}
+
+cudaError_t launch_segments(const ReqDev* d_reqs, const Item* d_items, int* d_next,
+                            const std::vector<Segment>& segs, cudaStream_t s, cudaStream_t aux,
+                            cudaEvent_t fork, cudaEvent_t join) {
+  const bool split = segs.size() > 1 && segs[0].launch.variant == kSmemVariant && aux;
+  cudaError_t e = cudaSuccess;
+  if (split) {
+    if ((e = cudaEventRecord(fork, s)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(aux, fork, 0)) != cudaSuccess) return e;
+  }
+  for (size_t i = 0; i < segs.size() && e == cudaSuccess; ++i) {
+    const Segment& g = segs[i];
+    cudaStream_t st = (split && i > 0) ? aux : s;
+    e = launch_batch_kernel(d_reqs, d_items + g.begin, g.count, d_next + i, g.launch, st);
+  }
+  if (e != cudaSuccess || !split) return e;
+  if ((e = cudaEventRecord(join, aux)) != cudaSuccess) return e;
+  return cudaStreamWaitEvent(s, join, 0);
 }
 
 int tuned_lanes(int k, int64_t n, int hub) {
@@ -300,16 +342,15 @@ struct mknn_batch {
   std::vector<mknn_batch_req> reqs;
   std::vector<int> lanes;        // chosen lanes per request
   ReqDev* d_reqs = nullptr;
-  // items of the one-lane requests (shared-memory kernel) and of the
-  // group requests (register kernel); each family has its own queue
-  Item* d_items = nullptr;       // [family A items | family B items]
-  int nitems_a = 0, nitems_b = 0;
-  int* d_next = nullptr;         // [0] queue A, [1] queue B
+  // work items grouped by kernel variant, one queue counter per segment
+  Item* d_items = nullptr;
+  int64_t nitems = 0;
+  std::vector<Segment> segs;
+  int* d_next = nullptr;         // [i] queue of segment i
   void* d_ws = nullptr;          // sort scratch: shared histogram, per-request cells and orders
   size_t ws_bytes = 0;
   std::vector<size_t> cell_off, perm_off;  // per request, 0 if not sorted
-  BatchLaunch launch_a, launch_b;
-  cudaStream_t aux = nullptr;    // second branch when both families are present
+  cudaStream_t aux = nullptr;    // second branch: the group segments
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -338,10 +379,9 @@ void free_plan(mknn_batch* b) {
 }
 
 // Enqueues the plan's work on stream s: the locality sorts, then the
-// persistent launch of each family present (the two run concurrently on
-// s and the plan's second stream when both are present).
+// persistent launch of each segment.
 cudaError_t enqueue(mknn_batch* b, cudaStream_t s) {
-  cudaError_t e = cudaMemsetAsync(b->d_next, 0, 2 * sizeof(int), s);
+  cudaError_t e = cudaMemsetAsync(b->d_next, 0, b->segs.size() * sizeof(int), s);
   if (e != cudaSuccess) return e;
   for (int r = 0; r < b->nreq; ++r) {
     if (!b->perm_off[r]) continue;
@@ -353,21 +393,8 @@ cudaError_t enqueue(mknn_batch* b, cudaStream_t s) {
                                 (int32_t*)((char*)b->d_ws + b->perm_off[r]), s);
     if (e != cudaSuccess) return e;
   }
-  const Item* items_a = b->d_items;
-  const Item* items_b = b->d_items + b->nitems_a;
-  if (b->nitems_a > 0 && b->nitems_b > 0) {
-    if ((e = cudaEventRecord(b->ev_fork, s)) != cudaSuccess) return e;
-    if ((e = cudaStreamWaitEvent(b->aux, b->ev_fork, 0)) != cudaSuccess) return e;
-    e = launch_batch_kernel(b->d_reqs, items_b, b->nitems_b, b->d_next + 1, b->launch_b, b->aux);
-    if (e != cudaSuccess) return e;
-    if ((e = cudaEventRecord(b->ev_join, b->aux)) != cudaSuccess) return e;
-    e = launch_batch_kernel(b->d_reqs, items_a, b->nitems_a, b->d_next, b->launch_a, s);
-    if (e != cudaSuccess) return e;
-    return cudaStreamWaitEvent(s, b->ev_join, 0);
-  }
-  if (b->nitems_a > 0)
-    return launch_batch_kernel(b->d_reqs, items_a, b->nitems_a, b->d_next, b->launch_a, s);
-  return launch_batch_kernel(b->d_reqs, items_b, b->nitems_b, b->d_next + 1, b->launch_b, s);
+  return launch_segments(b->d_reqs, b->d_items, b->d_next, b->segs, s, b->aux, b->ev_fork,
+                         b->ev_join);
 }
 
 }  // namespace
@@ -439,18 +466,17 @@ mknn_status mknn_batch_create(const mknn_batch_req* reqs, int32_t nreq,
   std::vector<int> orderq(nreq);
   for (int r = 0; r < nreq; ++r) orderq[r] = r;
   std::stable_sort(orderq.begin(), orderq.end(), [&](int a, int c) { return cost[a] > cost[c]; });
-  std::vector<Item> items;       // family A (one lane, shared memory) first, then B
-  for (int fam = 0; fam < 2; ++fam) {
-    for (int r : orderq) {
-      if ((b->lanes[r] == 1) != (fam == 0)) continue;
-      const int v = variant_index(b->lanes[r], reqs[r].k);
-      const int per = item_queries(b->lanes[r], rounds);
-      for (int64_t s0 = 0; s0 < reqs[r].nq; s0 += per)
-        items.push_back(Item{r, (int32_t)s0, (int32_t)std::min<int64_t>(reqs[r].nq, s0 + per), v});
-    }
-    if (fam == 0) b->nitems_a = (int)items.size();
+  std::vector<Item> items;
+  int kcap = 0;
+  for (int r : orderq) {
+    const int v = variant_index(b->lanes[r], reqs[r].k);
+    const int per = item_queries(b->lanes[r], rounds);
+    if (v == kSmemVariant) kcap = std::max(kcap, (int)reqs[r].k);
+    for (int64_t s0 = 0; s0 < reqs[r].nq; s0 += per)
+      items.push_back(Item{r, (int32_t)s0, (int32_t)std::min<int64_t>(reqs[r].nq, s0 + per), v});
   }
-  b->nitems_b = (int)items.size() - b->nitems_a;
+  b->segs = make_segments(items, o.blocks_per_sm, kcap);
+  b->nitems = (int64_t)items.size();
   cudaError_t e;
   if ((e = cudaMalloc((void**)&b->d_reqs, sizeof(ReqDev) * std::max(nreq, 1))) != cudaSuccess ||
       (e = cudaMalloc((void**)&b->d_items, sizeof(Item) * std::max<size_t>(items.size(), 1))) !=
@@ -472,12 +498,7 @@ mknn_status mknn_batch_create(const mknn_batch_req* reqs, int32_t nreq,
     free_plan(raw);
     return bfail(MKNN_ECUDA, std::string("plan upload: ") + cudaGetErrorString(e));
   }
-  int kcap = 0;
-  for (int r = 0; r < nreq; ++r)
-    if (b->lanes[r] == 1) kcap = std::max(kcap, (int)reqs[r].k);
-  b->launch_a = batch_config(b->nitems_a, o.blocks_per_sm, kcap, true);
-  b->launch_b = batch_config(b->nitems_b, o.blocks_per_sm, 0, false);
-  if (b->nitems_a > 0 && b->nitems_b > 0) {
+  if (b->segs.size() > 1 && b->segs[0].launch.variant == kSmemVariant) {
     if ((e = cudaStreamCreateWithFlags(&b->aux, cudaStreamNonBlocking)) != cudaSuccess ||
         (e = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming)) != cudaSuccess ||
         (e = cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming)) != cudaSuccess) {
@@ -529,9 +550,12 @@ mknn_status mknn_batch_info(const mknn_batch* b, int32_t* lanes_out, int64_t* it
   if (!b) return bfail(MKNN_EINVAL, "plan is NULL");
   if (lanes_out)
     for (int r = 0; r < b->nreq; ++r) lanes_out[r] = b->lanes[r];
-  if (items) *items = (int64_t)b->nitems_a + b->nitems_b;
-  if (grid)
-    *grid = (b->nitems_a > 0 ? b->launch_a.grid : 0) + (b->nitems_b > 0 ? b->launch_b.grid : 0);
+  if (items) *items = b->nitems;
+  if (grid) {
+    int g = 0;
+    for (const Segment& sg : b->segs) g += sg.launch.grid;
+    *grid = g;
+  }
   return MKNN_OK;
 }
 
@@ -662,6 +686,12 @@ mknn_status mknn_tune_save(const char* path) {
   for (auto& kv : g_tune)
     std::fprintf(f, "%d %d %d %d\n", kv.first.k, kv.first.nbucket, kv.first.hub, kv.second);
   return std::fclose(f) == 0 ? MKNN_OK : bfail(MKNN_EIO, "write failed");
+}
+
+mknn_status mknn_tune_clear(void) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune.clear();
+  return MKNN_OK;
 }
 
 mknn_status mknn_tune_load(const char* path) {

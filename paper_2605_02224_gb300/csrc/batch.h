@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <vector>
 
 namespace mknn {
 
@@ -35,18 +36,39 @@ int variant_index(int lanes, int k);
 // Queries per work item for the given lanes and rounds per item.
 inline int item_queries(int lanes, int rounds) { return (32 / lanes) * rounds; }
 
-// Shape of one persistent launch.
+// Variant index of the one-lane shared-memory kernel.
+constexpr int kSmemVariant = 12;
+
+// Shape of one persistent launch: one kernel variant over a queue of items.
 struct BatchLaunch {
   int grid = 1, threads = 256;
   size_t smem = 0;    // dynamic shared memory for the one-lane candidate lists
-  int kcap = 0;       // list capacity: the largest k among one-lane requests (0: none)
-  bool smem_only = false;  // every request uses the one-lane shared-memory variant
+  int kcap = 0;       // list capacity: the largest k among one-lane requests
+  int variant = kSmemVariant;
 };
-// Grid, block and shared memory for `nitems` items.
-BatchLaunch batch_config(int nitems, int blocks_per_sm, int kcap, bool smem_only);
-// Launches the persistent kernel; *d_next must be zero on entry.
+// Grid, block and shared memory for `nitems` items of one variant.
+BatchLaunch batch_config(int nitems, int blocks_per_sm, int kcap, int variant);
+// Launches the persistent kernel of b.variant; *d_next must be zero on entry.
 cudaError_t launch_batch_kernel(const ReqDev* d_reqs, const Item* d_items, int nitems, int* d_next,
                                 const BatchLaunch& b, cudaStream_t s);
+
+// The items of one variant: a contiguous range of the item array with its
+// own queue counter and launch.
+struct Segment {
+  int begin = 0, count = 0;
+  BatchLaunch launch;
+};
+// Reorders items by variant (the one-lane kernel's first, each variant's
+// items in their given order) and returns one segment per variant present.
+std::vector<Segment> make_segments(std::vector<Item>& items, int blocks_per_sm, int kcap);
+// Launches every segment, segment i draining the queue counter d_next[i]
+// (zero on entry). With one-lane and group segments both present, the
+// group segments run one after another on `aux`, forked from s and joined
+// back, concurrently with the one-lane segment on s; otherwise all run on
+// s in order.
+cudaError_t launch_segments(const ReqDev* d_reqs, const Item* d_items, int* d_next,
+                            const std::vector<Segment>& segs, cudaStream_t s, cudaStream_t aux,
+                            cudaEvent_t fork, cudaEvent_t join);
 
 // Lanes per query recorded by the tuner for (k, floor(log2 n)), 0 if none.
 // The tuning table is keyed by k, floor(log2 n) and the cloud's hub bucket

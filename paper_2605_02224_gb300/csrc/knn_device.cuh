@@ -502,56 +502,52 @@ __device__ __forceinline__ void knn_query_thread(const CloudDev& C, float qx, fl
 
 // ---------------------------------------------------------------------------
 // One query per thread with the candidate list N sorted in shared memory:
-// entry i of the lane's list at base[i * 32] (a warp's lists interleaved,
-// so any mix of positions across the lanes is bank-conflict free). An
-// insertion is a binary search - which also finds an equal key, so the
-// membership test of Alg. 2 costs nothing extra - and a shift of the
-// tail; the nearest not-yet-expanded entry among the first k-1 is one bit
-// scan of the expanded mask; the output is already in order. The list
-// takes no registers, which leaves room for more resident warps.
-struct SmemList {
-  float* d;        // this lane's column: d[i * 32]
-  uint32_t* r;
-  int cnt;
-  uint64_t done;   // bit i: entry at position i expanded
-  float wd;        // key of position k-1 (a pad while cnt < k)
-  uint32_t wr;
-};
-
-__device__ __forceinline__ void slist_init(SmemList& L, float* dcol, uint32_t* rcol) {
-  L.d = dcol;
-  L.r = rcol;
-  L.cnt = 0;
-  L.done = 0ull;
-  L.wd = __int_as_float(0x7f800000);
-  L.wr = kRankMask;
+// entry i of the lane's list at col[i * 32] (a warp's lists interleaved, so
+// any mix of positions across the lanes is bank-conflict free). An entry is
+// one 64-bit key, the float bits of the squared distance above the rank:
+// distances are never negative, so the integer order of the keys is the
+// (distance, rank) order and a comparison, a load or a move is one
+// instruction. An insertion is a binary search - which also finds an equal
+// key, so the membership test of Alg. 2 costs nothing extra - and a shift
+// of the tail; the nearest not-yet-expanded entry among the first k-1 is
+// one bit scan of the expanded mask; the output is already in order. The
+// list takes no registers, which leaves room for more resident warps.
+__device__ __forceinline__ uint64_t pack_key(float d, uint32_t r) {
+  return ((uint64_t)__float_as_uint(d) << 32) | r;
 }
 
-// Inserts (cd, cr) if not present; caller checks key_lt(cd, cr, L.wd, L.wr).
-__device__ __forceinline__ void slist_insert(SmemList& L, float cd, uint32_t cr, int k) {
+struct SmemList {
+  uint64_t* col;   // this lane's column: col[i * 32]
+  int cnt;
+  uint64_t done;   // bit i: entry at position i expanded
+  uint64_t worst;  // key of position k-1 (a pad while cnt < k)
+};
+
+__device__ __forceinline__ void slist_init(SmemList& L, uint64_t* col) {
+  L.col = col;
+  L.cnt = 0;
+  L.done = 0ull;
+  L.worst = pack_key(__int_as_float(0x7f800000), kRankMask);
+}
+
+// Inserts key c if not present; caller checks c < L.worst.
+__device__ __forceinline__ void slist_insert(SmemList& L, uint64_t c, int k) {
   int lo = 0, hi = L.cnt;
   while (lo < hi) {
     const int mid = (lo + hi) >> 1;
-    if (key_lt(L.d[mid * 32], L.r[mid * 32], cd, cr))
+    if (L.col[mid * 32] < c)
       lo = mid + 1;
     else
       hi = mid;
   }
   const int pos = lo;
-  if (pos < L.cnt && L.d[pos * 32] == cd && L.r[pos * 32] == cr) return;
-  for (int i = min(L.cnt, k - 1); i > pos; --i) {
-    L.d[i * 32] = L.d[(i - 1) * 32];
-    L.r[i * 32] = L.r[(i - 1) * 32];
-  }
-  L.d[pos * 32] = cd;
-  L.r[pos * 32] = cr;
+  if (pos < L.cnt && L.col[pos * 32] == c) return;
+  for (int i = min(L.cnt, k - 1); i > pos; --i) L.col[i * 32] = L.col[(i - 1) * 32];
+  L.col[pos * 32] = c;
   const uint64_t low = pos ? (L.done & (~0ull >> (64 - pos))) : 0ull;
   L.done = low | ((L.done >> pos) << 1 << pos);
   if (L.cnt < k) L.cnt++;
-  if (L.cnt == k) {
-    L.wd = L.d[(k - 1) * 32];
-    L.wr = L.r[(k - 1) * 32];
-  }
+  if (L.cnt == k) L.worst = L.col[(k - 1) * 32];
 }
 
 // Descent decision: is the candidate at squared distance d (site ps)
@@ -577,13 +573,13 @@ __device__ __forceinline__ bool strictly_closer(float qx, float qy, float qz, fl
 // 1.3x-2x faster than the row-by-row loop nest). The index of the next
 // entry is loaded one iteration ahead.
 __device__ __forceinline__ void knn_query_smem(const CloudDev& C, float qx, float qy, float qz,
-                                               int k, int m, float* dcol, uint32_t* rcol,
+                                               int k, int m, uint64_t* col,
                                                int32_t* __restrict__ oi, float* __restrict__ od) {
   SmemList L;
-  slist_init(L, dcol, rcol);
+  slist_init(L, col);
   float4 pc = __ldg(C.pts);
   float dcur = sqd32(qx, qy, qz, pc);
-  slist_insert(L, dcur, 0u, k);
+  slist_insert(L, pack_key(dcur, 0u), k);
   bool desc = true;
   int e = __ldg(C.rowp), end = __ldg(C.rowp + 1);
   int s_next = e < end ? __ldg(C.succ + e) : 0x7fffffff;
@@ -594,17 +590,18 @@ __device__ __forceinline__ void knn_query_smem(const CloudDev& C, float qx, floa
       s_next = e < end ? __ldg(C.succ + e) : 0x7fffffff;
       const float4 ps = __ldg(C.pts + s);
       const float d = sqd32(qx, qy, qz, ps);
+      const uint64_t key = pack_key(d, (uint32_t)s);
       if (desc) {
         if (strictly_closer(qx, qy, qz, d, ps, dcur, pc)) {
           dcur = d;
           pc = ps;
-          if (key_lt(d, (uint32_t)s, L.wd, L.wr)) slist_insert(L, d, (uint32_t)s, k);
+          if (key < L.worst) slist_insert(L, key, k);
           e = __ldg(C.rowp + s);
           end = __ldg(C.rowp + s + 1);
           s_next = e < end ? __ldg(C.succ + e) : 0x7fffffff;
         }
-      } else if (key_lt(d, (uint32_t)s, L.wd, L.wr)) {
-        slist_insert(L, d, (uint32_t)s, k);
+      } else if (key < L.worst) {
+        slist_insert(L, key, k);
       }
       continue;
     }
@@ -615,15 +612,16 @@ __device__ __forceinline__ void knn_query_smem(const CloudDev& C, float qx, floa
     if (!cand) break;
     const int pos = __ffsll((long long)cand) - 1;
     L.done |= 1ull << pos;
-    const int site = (int)L.r[pos * 32];
+    const int site = (int)(uint32_t)L.col[pos * 32];
     e = __ldg(C.rowp + site);
     end = __ldg(C.rowp + site + 1);
     s_next = e < end ? __ldg(C.succ + e) : 0x7fffffff;
   }
   for (int p = 0; p < k; ++p) {
     const bool real = p < L.cnt;
-    oi[p] = real ? (int32_t)L.r[p * 32] : -1;
-    od[p] = real ? L.d[p * 32] : __int_as_float(0x7f800000);
+    const uint64_t key = real ? L.col[p * 32] : 0ull;
+    oi[p] = real ? (int32_t)(uint32_t)key : -1;
+    od[p] = real ? __uint_as_float((uint32_t)(key >> 32)) : __int_as_float(0x7f800000);
   }
 }
 

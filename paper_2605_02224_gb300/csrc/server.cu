@@ -230,9 +230,9 @@ void mknn_server::launch(Slot& sl, std::vector<uint64_t>& tickets, size_t off, s
     const size_t reqs_off = 256 + kSortHistBytes;
     const int nreq = (int)tickets.size();
     std::vector<ReqDev> rd(nreq);
-    std::vector<Item> items_a, items_b;  // one-lane requests | group requests
+    std::vector<Item> items;
     int kcap = 0;
-    int64_t pack_nq = 0;  // the pack runs as one launch per family: its size sets the lanes
+    int64_t pack_nq = 0;  // the pack runs as one launch per variant: its size sets the lanes
     for (int i = 0; i < nreq; ++i) pack_nq += recs[tickets[i] - 1].r.nq;
     for (int i = 0; i < nreq; ++i) {
       ReqRec& R = recs[tickets[i] - 1];
@@ -259,41 +259,25 @@ void mknn_server::launch(Slot& sl, std::vector<uint64_t>& tickets, size_t off, s
                      q.m ? q.m : (int32_t)c->n};
       const int v = variant_index(lanes, q.k);
       const int per = item_queries(lanes, 8);
-      if (lanes == 1) kcap = std::max(kcap, (int)q.k);
-      std::vector<Item>& dst = lanes == 1 ? items_a : items_b;
+      if (v == kSmemVariant) kcap = std::max(kcap, (int)q.k);
       for (int64_t b0 = 0; b0 < q.nq; b0 += per)
-        dst.push_back(Item{i, (int32_t)b0, (int32_t)std::min<int64_t>(q.nq, b0 + per), v});
+        items.push_back(Item{i, (int32_t)b0, (int32_t)std::min<int64_t>(q.nq, b0 + per), v});
     }
-    const int na = (int)items_a.size(), nb = (int)items_b.size();
+    const std::vector<Segment> segs = make_segments(items, 0, kcap);
+    const size_t ni = items.size();
     const size_t items_off = reqs_off + al(sizeof(ReqDev) * nreq);
     // request table and items go through the pinned mirror
     std::memcpy(hbase + reqs_off, rd.data(), sizeof(ReqDev) * nreq);
-    std::memcpy(hbase + items_off, items_a.data(), sizeof(Item) * na);
-    std::memcpy(hbase + items_off + sizeof(Item) * na, items_b.data(), sizeof(Item) * nb);
+    std::memcpy(hbase + items_off, items.data(), sizeof(Item) * ni);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(dbase + reqs_off, hbase + reqs_off,
-                          items_off - reqs_off + sizeof(Item) * (na + nb),
-                          cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(d_next, 0, 2 * sizeof(int), s);
-    const ReqDev* d_reqs = (const ReqDev*)(dbase + reqs_off);
-    const Item* d_items = (const Item*)(dbase + items_off);
-    if (e == cudaSuccess && na > 0 && nb > 0) {
-      // both families: the group kernel runs on the slot's second stream,
-      // concurrently with the one-lane kernel, and joins before the copies
-      e = cudaEventRecord(sl.fork, s);
-      if (e == cudaSuccess) e = cudaStreamWaitEvent(sl.aux, sl.fork, 0);
-      if (e == cudaSuccess)
-        e = launch_batch_kernel(d_reqs, d_items + na, nb, d_next + 1,
-                                batch_config(nb, 0, 0, false), sl.aux);
-      if (e == cudaSuccess) e = cudaEventRecord(sl.join, sl.aux);
-      if (e == cudaSuccess)
-        e = launch_batch_kernel(d_reqs, d_items, na, d_next, batch_config(na, 0, kcap, true), s);
-      if (e == cudaSuccess) e = cudaStreamWaitEvent(s, sl.join, 0);
-    } else if (e == cudaSuccess && na > 0) {
-      e = launch_batch_kernel(d_reqs, d_items, na, d_next, batch_config(na, 0, kcap, true), s);
-    } else if (e == cudaSuccess) {
-      e = launch_batch_kernel(d_reqs, d_items, nb, d_next + 1, batch_config(nb, 0, 0, false), s);
-    }
+                          items_off - reqs_off + sizeof(Item) * ni, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_next, 0, segs.size() * sizeof(int), s);
+    // the one-lane kernel on the slot's stream, the group kernels on its
+    // second stream, joined before the copies back
+    if (e == cudaSuccess)
+      e = launch_segments((const ReqDev*)(dbase + reqs_off), (const Item*)(dbase + items_off),
+                          d_next, segs, s, sl.aux, sl.fork, sl.join);
     for (int i = 0; i < nreq && e == cudaSuccess; ++i) {
       ReqRec& R = recs[tickets[i] - 1];
       const size_t nk = (size_t)R.r.nq * R.r.k * 4;

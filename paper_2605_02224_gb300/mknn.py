@@ -132,6 +132,7 @@ def _declare(L):
         "mknn_batch_tune": (i32, [vp, i32, i64, vp]),
         "mknn_tune_save": (i32, [C.c_char_p]),
         "mknn_tune_load": (i32, [C.c_char_p]),
+        "mknn_tune_clear": (i32, []),
         "mknn_server_create": (i32, [vp, pp]),
         "mknn_server_add_cloud": (i32, [vp, vp, vp]),
         "mknn_server_submit": (i32, [vp, vp, vp]),
@@ -379,6 +380,10 @@ def mknn_tune_save(path: str):
 
 def mknn_tune_load(path: str):
     _check(lib().mknn_tune_load(path.encode()))
+
+
+def mknn_tune_clear():
+    _check(lib().mknn_tune_clear())
 
 
 # ---------------------------------------------------------------- serving

@@ -78,6 +78,38 @@ def test_batch_equals_plain_per_request(torch, clouds, lanes):
         assert np.array_equal(d2.cpu().numpy(), pd), wl.name
 
 
+def test_plan_with_many_variants_equals_plain(torch, clouds, tmp_path):
+    """A tuning table that gives the eight requests different lane widths:
+    the plan runs one persistent launch per variant (one-lane kernel and
+    group kernels on two streams), and every row equals a plain launch."""
+    reqs, keep = _requests(torch, clouds, "array")
+    widths = (1, 32, 8, 16, 1, 32, 16, 8)
+    lines = []
+    for (wl, c, *_), w in zip(keep, widths):
+        longest = int(np.diff(c.table()[1]).max())
+        lines.append(f"{wl.k} {int(np.floor(np.log2(wl.n)))} "
+                     f"{int(np.floor(np.log2(1 + longest)))} {w}\n")
+    path = tmp_path / "table.txt"
+    path.write_text("# k log2n hub lanes\n" + "".join(lines))
+    M.mknn_tune_clear()
+    M.mknn_tune_load(str(path))
+    try:
+        plan = M.mknn_batch_create(reqs)
+        lanes, items, grid = M.mknn_batch_info(plan, len(reqs))
+        assert len(set(lanes.tolist())) >= 3, lanes
+        s = torch.cuda.current_stream().cuda_stream
+        for _ in range(2):                           # graph replay twice
+            M.mknn_batch_run(plan, s)
+        torch.cuda.synchronize()
+        for wl, c, q, m, ms, idx, d2 in keep:
+            pi, pd = _plain(torch, c, q, wl.k, m, ms)
+            assert np.array_equal(idx.cpu().numpy(), pi), wl.name
+            assert np.array_equal(d2.cpu().numpy(), pd), wl.name
+        M.mknn_batch_free(plan)
+    finally:
+        M.mknn_tune_clear()
+
+
 def test_batch_against_oracle_sample(torch, clouds):
     reqs, keep = _requests(torch, clouds, "array")
     plan = M.mknn_batch_create(reqs)
