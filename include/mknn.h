@@ -259,7 +259,8 @@ typedef struct {
 typedef struct {
   int32_t lanes;          /* 0 = tuned per request, else 4, 8, 16 or 32 for all */
   int32_t sort;           /* 0 = sort requests with >= 4096 queries, 1 = all, -1 = none */
-  int32_t item_rounds;    /* rounds of the group width per work item (0 = 8) */
+  int32_t item_rounds;    /* rounds of the group width per work item (0 = 8,
+                             fewer for a plan too small to fill the GPU) */
   int32_t blocks_per_sm;  /* 0 = occupancy limit */
   int32_t graph;          /* 0 = capture a CUDA graph (default), -1 = plain launches */
   int32_t reserved[7];

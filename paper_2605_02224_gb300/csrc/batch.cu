@@ -203,6 +203,12 @@ int fill_lanes(int64_t nq, int k) {
   return lanes;
 }
 
+int auto_item_rounds(int64_t warp_rounds) {
+  // two items per resident warp (40 per SM at 48 registers) before rounds grow
+  const int64_t target = (int64_t)num_sms() * 40 * 2;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(8, warp_rounds / target));
+}
+
 int choose_lanes(int k, int64_t n, int hub, int64_t nq) {
   const int t = tuned_lanes(k, n, hub);
   int lanes = std::max(t ? t : heuristic_lanes(k, hub), fill_lanes(nq, k));
@@ -412,7 +418,6 @@ mknn_status mknn_batch_create(const mknn_batch_req* reqs, int32_t nreq,
   cudaGetDevice(&dev);
   mknn_batch_opts o{};
   if (opts) o = *opts;
-  const int rounds = o.item_rounds > 0 ? o.item_rounds : 8;
   std::unique_ptr<mknn_batch> b(new mknn_batch());
   b->device = dev;
   b->nreq = nreq;
@@ -466,6 +471,9 @@ mknn_status mknn_batch_create(const mknn_batch_req* reqs, int32_t nreq,
   std::vector<int> orderq(nreq);
   for (int r = 0; r < nreq; ++r) orderq[r] = r;
   std::stable_sort(orderq.begin(), orderq.end(), [&](int a, int c) { return cost[a] > cost[c]; });
+  int64_t warp_rounds = 0;
+  for (int r = 0; r < nreq; ++r) warp_rounds += (reqs[r].nq * b->lanes[r] + 31) / 32;
+  const int rounds = o.item_rounds > 0 ? o.item_rounds : auto_item_rounds(warp_rounds);
   std::vector<Item> items;
   int kcap = 0;
   for (int r : orderq) {

@@ -35,6 +35,11 @@ struct Item {
 int variant_index(int lanes, int k);
 // Queries per work item for the given lanes and rounds per item.
 inline int item_queries(int lanes, int rounds) { return (32 / lanes) * rounds; }
+// Rounds per item for a launch whose requests need `warp_rounds` warp
+// rounds in all (sum over requests of ceil(nq * lanes / 32)): 8, or fewer
+// when that would leave too few items to keep every SM's warps busy (a
+// small pack is cut finer so its latency stays that of a plain launch).
+int auto_item_rounds(int64_t warp_rounds);
 
 // Variant index of the one-lane shared-memory kernel.
 constexpr int kSmemVariant = 12;

@@ -123,7 +123,13 @@ bool is_pinned(const void* p) {
 
 size_t request_bytes(int64_t nq, int k) {
   return al((size_t)nq * 12) + 2 * al((size_t)nq * 4) + 2 * al((size_t)nq * k * 4) +
-         sizeof(ReqDev) + sizeof(Item) * (size_t)(nq / 8 + 2);
+         sizeof(ReqDev);
+}
+
+// Room for the work items of a pack: at most one item per query and one
+// partial item per request (items may be as small as one query).
+size_t items_bytes(int64_t nq_total, size_t nreq) {
+  return al(sizeof(Item) * ((size_t)nq_total + 2 * nreq + 64));
 }
 
 constexpr size_t kPackFixed = kSortHistBytes + 1024;  // histogram, tile totals, counter
@@ -234,6 +240,15 @@ void mknn_server::launch(Slot& sl, std::vector<uint64_t>& tickets, size_t off, s
     int kcap = 0;
     int64_t pack_nq = 0;  // the pack runs as one launch per variant: its size sets the lanes
     for (int i = 0; i < nreq; ++i) pack_nq += recs[tickets[i] - 1].r.nq;
+    std::vector<int> lanes(nreq);
+    int64_t warp_rounds = 0;
+    for (int i = 0; i < nreq; ++i) {
+      const mknn_request& q = recs[tickets[i] - 1].r;
+      const mknn_cloud* c = clouds[q.cloud];
+      lanes[i] = o.lanes ? o.lanes : choose_lanes(q.k, c->n, c->hub_bucket(), pack_nq);
+      warp_rounds += (q.nq * lanes[i] + 31) / 32;
+    }
+    const int rounds = auto_item_rounds(warp_rounds);
     for (int i = 0; i < nreq; ++i) {
       ReqRec& R = recs[tickets[i] - 1];
       const mknn_request& q = R.r;
@@ -251,14 +266,13 @@ void mknn_server::launch(Slot& sl, std::vector<uint64_t>& tickets, size_t off, s
         e = launch_query_sort_split(cd, (const float*)(dbase + R.q_off), 3, q.nq, d_hist,
                                     (int32_t*)(dbase + R.cell_off), (int32_t*)(dbase + R.perm_off),
                                     s);
-      const int lanes = o.lanes ? o.lanes : choose_lanes(q.k, c->n, c->hub_bucket(), pack_nq);
       rd[i] = ReqDev{(const float4*)cd.pts, cd.rowp, cd.succ, cd.n, 3,
                      (const float*)(dbase + R.q_off), nullptr,
                      sorted ? (const int32_t*)(dbase + R.perm_off) : nullptr,
                      (int32_t*)(dbase + R.idx_off), (float*)(dbase + R.d2_off), c->d_err, q.k,
                      q.m ? q.m : (int32_t)c->n};
-      const int v = variant_index(lanes, q.k);
-      const int per = item_queries(lanes, 8);
+      const int v = variant_index(lanes[i], q.k);
+      const int per = item_queries(lanes[i], rounds);
       if (v == kSmemVariant) kcap = std::max(kcap, (int)q.k);
       for (int64_t b0 = 0; b0 < q.nq; b0 += per)
         items.push_back(Item{i, (int32_t)b0, (int32_t)std::min<int64_t>(q.nq, b0 + per), v});
@@ -320,7 +334,7 @@ void mknn_server::run() {
       const ReqRec& R = recs[t - 1];
       const size_t rb = request_bytes(R.r.nq, R.r.k);
       const size_t meta = o.plain ? 0 : al(sizeof(ReqDev) * (take.size() + 1)) +
-                                            al(sizeof(Item) * (size_t)(nq_total + R.r.nq) / 8 + 64);
+                                            items_bytes(nq_total + R.r.nq, take.size() + 1);
       if (!take.empty() && (bytes + rb + meta > room || nq_total + R.r.nq > o.max_batch_queries))
         break;
       if (take.empty() && bytes + rb + meta > room) break;  // wait for memory
@@ -332,7 +346,7 @@ void mknn_server::run() {
     if (take.empty()) continue;
     const size_t meta = o.plain ? kSortHistBytes + 256
                                 : al(sizeof(ReqDev) * take.size()) +
-                                      al(sizeof(Item) * ((size_t)nq_total / 4 + 64 * take.size()));
+                                      items_bytes(nq_total, take.size());
     bytes += meta;
     size_t off = 0;
     if (!arena.alloc(bytes, &off)) continue;
@@ -350,7 +364,7 @@ void mknn_server::run() {
       R.d2_off = c;
     } else {
       size_t c = 256 + kSortHistBytes + al(sizeof(ReqDev) * take.size()) +
-                 al(sizeof(Item) * ((size_t)nq_total / 4 + 64 * take.size()));
+                 items_bytes(nq_total, take.size());
       for (uint64_t t : take) {
         ReqRec& R = recs[t - 1];
         const int64_t nq = R.r.nq;
@@ -445,8 +459,7 @@ mknn_status mknn_server_submit(mknn_server* s, const mknn_request* r, uint64_t* 
   if (r->nq < 1 || r->nq >= (int64_t)0x7FFFFFFF || r->k < 1 || r->k > MKNN_MAX_K ||
       r->m < 0 || r->m > c->n || !r->q || !r->out_idx || !r->out_d2)
     return sfail(MKNN_EINVAL, "bad request (nq, k, m or NULL buffer)");
-  const size_t need = request_bytes(r->nq, r->k) + al(kPackFixed) + 4096 +
-                      al(sizeof(Item) * ((size_t)r->nq / 4 + 64));
+  const size_t need = request_bytes(r->nq, r->k) + al(kPackFixed) + 4096 + items_bytes(r->nq, 1);
   if (need > s->arena_bytes)
     return sfail(MKNN_ENOMEM, "request alone exceeds the server's memory budget");
   lk.unlock();
