@@ -92,9 +92,11 @@ mknn_status mknn_cloud_from_table(const float* xyz_ranked, int64_t n, const int6
                                   const int32_t* succ, mknn_cloud** out);
 
 /* Copies coordinates (as float4 x,y,z,0 in rank order) and the CSR table to
- * the current device. Idempotent; synchronous with respect to the host
- * (the copies complete before return). Device bytes: 16 n + 4 (n+1) + 4 E
- * plus a few words of status. Errors: ENOMEM, ECUDA. */
+ * the current device, and builds there a second copy of the successor
+ * entries with each entry's site inlined (float4 x, y, z, rank), which the
+ * query kernels read with one load per entry. Idempotent; synchronous with
+ * respect to the host (the copies complete before return). Device bytes:
+ * 16 n + 4 (n+1) + 20 E plus a few words of status. Errors: ENOMEM, ECUDA. */
 mknn_status mknn_cloud_upload(mknn_cloud* cloud, mknn_stream_t stream);
 
 /* Releases device memory of the cloud (keeps the host copy). */

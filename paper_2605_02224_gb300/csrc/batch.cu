@@ -71,7 +71,7 @@ __device__ __forceinline__ uint64_t* smem_column(int kcap) {
 
 __device__ __forceinline__ void serve_item_smem(const ReqDev& R, const Item& w, uint64_t* col) {
   const int lane = (int)(threadIdx.x & 31u);
-  const CloudDev C{R.pts, R.rowp, R.succ, R.n};
+  const CloudDev C{R.pts, R.rowp, R.succ, R.n, R.ent};
   for (int i = w.begin + lane; i < w.end; i += 32) {
     const int64_t qi = R.perm ? (int64_t)__ldg(R.perm + i) : (int64_t)i;
     const float* qp = R.q + qi * R.q_stride;
@@ -96,7 +96,7 @@ __device__ __forceinline__ void serve_item(const ReqDev& R, const Item& w) {
   const Grp<G> g;
   const int gi = (int)((threadIdx.x & 31u) / G);
   constexpr int kGroups = 32 / G;
-  const CloudDev C{R.pts, R.rowp, R.succ, R.n};
+  const CloudDev C{R.pts, R.rowp, R.succ, R.n, R.ent};
   for (int i = w.begin + gi; i < w.end; i += kGroups) {
     const int64_t qi = R.perm ? (int64_t)__ldg(R.perm + i) : (int64_t)i;
     const float* qp = R.q + qi * R.q_stride;
@@ -452,7 +452,7 @@ mknn_status mknn_batch_create(const mknn_batch_req* reqs, int32_t nreq,
     const CloudDevHost cd = R.cloud->dev();
     rd[r] = ReqDev{(const float4*)cd.pts, cd.rowp,   cd.succ, cd.n,  R.q_stride,
                    R.q,                   R.m,       nullptr, R.out_idx,
-                   R.out_d2,              R.cloud->d_err, R.k, ms};
+                   R.out_d2,              R.cloud->d_err, R.k, ms, (const float4*)cd.ent};
     cost[r] = (double)R.k * std::log2((double)R.cloud->n + 2.0);
     b->total_queries += R.nq;
   }

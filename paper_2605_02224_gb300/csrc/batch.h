@@ -23,6 +23,7 @@ struct ReqDev {
   int32_t* err;
   int32_t k;
   int32_t m_scalar;
+  const float4* ent;   // the cloud's successor entries with sites inlined
 };
 
 // A contiguous range of one request's queries (in processing order),

@@ -59,10 +59,12 @@ void free_device(mknn_cloud* c) {
     cudaFree(c->d_pts);
     cudaFree(c->d_rowp);
     cudaFree(c->d_succ);
+    cudaFree(c->d_ent);
     cudaFree(c->d_err);
     cudaSetDevice(cur);
   }
   c->d_pts = nullptr;
+  c->d_ent = nullptr;
   c->d_rowp = c->d_succ = c->d_err = nullptr;
   c->device = -1;
   c->dev_bytes = 0;
@@ -261,10 +263,12 @@ mknn_status mknn_cloud_upload(mknn_cloud* c, mknn_stream_t stream) {
   for (int64_t i = 0; i <= n; ++i) rp32[i] = (int32_t)c->rowp[i];
   c->device = cur;
   const size_t b_pts = (size_t)n * 16, b_rowp = (size_t)(n + 1) * 4,
-               b_succ = (size_t)std::max<int64_t>(E, 1) * 4;
+               b_succ = (size_t)std::max<int64_t>(E, 1) * 4,
+               b_ent = (size_t)std::max<int64_t>(E, 1) * 16;
   if ((e = cudaMalloc(&c->d_pts, b_pts)) != cudaSuccess ||
       (e = cudaMalloc((void**)&c->d_rowp, b_rowp)) != cudaSuccess ||
       (e = cudaMalloc((void**)&c->d_succ, b_succ)) != cudaSuccess ||
+      (e = cudaMalloc(&c->d_ent, b_ent)) != cudaSuccess ||
       (e = cudaMalloc((void**)&c->d_err, 256)) != cudaSuccess) {
     cudaGetLastError();
     free_device(c);
@@ -276,12 +280,13 @@ mknn_status mknn_cloud_upload(mknn_cloud* c, mknn_stream_t stream) {
           cudaSuccess ||
       (E > 0 && (e = cudaMemcpyAsync(c->d_succ, c->succ.data(), (size_t)E * 4,
                                      cudaMemcpyHostToDevice, s)) != cudaSuccess) ||
+      (E > 0 && (e = launch_fill_entries(c->d_pts, c->d_succ, E, c->d_ent, s)) != cudaSuccess) ||
       (e = cudaMemsetAsync(c->d_err, 0, 256, s)) != cudaSuccess ||
       (e = cudaStreamSynchronize(s)) != cudaSuccess) {
     free_device(c);
     return cuda_fail(e, "upload");
   }
-  c->dev_bytes = b_pts + b_rowp + b_succ + 256;
+  c->dev_bytes = b_pts + b_rowp + b_succ + b_ent + 256;
   return MKNN_OK;
 }
 

@@ -24,6 +24,7 @@ struct mknn_cloud {
   void* d_pts = nullptr;         // float4[n]
   int32_t* d_rowp = nullptr;     // [n+1]
   int32_t* d_succ = nullptr;     // [E]
+  void* d_ent = nullptr;         // float4[E]: succ with the sites' coordinates inlined
   int32_t* d_err = nullptr;      // error flags
   size_t dev_bytes = 0;
   std::atomic<int> holders{0};   // servers referencing the cloud
@@ -48,6 +49,7 @@ struct mknn_cloud {
     c.pts = d_pts;
     c.rowp = d_rowp;
     c.succ = d_succ;
+    c.ent = d_ent;
     c.n = (int32_t)n;
     for (int i = 0; i < 3; ++i) {
       c.lo[i] = lo[i];

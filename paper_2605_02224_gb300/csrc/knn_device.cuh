@@ -46,6 +46,9 @@ struct CloudDev {
   const int32_t* __restrict__ rowp;
   const int32_t* __restrict__ succ;
   int32_t n;
+  // succ with each entry's site inlined: (x, y, z, rank bits), one 16-byte
+  // load per entry instead of an index load and a dependent point load
+  const float4* __restrict__ ent;
 };
 
 // Squared distance in float32, fixed operation order (no reassociation).
@@ -202,14 +205,11 @@ __device__ __forceinline__ void knn_query(const CloudDev& C, const Grp<G>& g, fl
     for (int base = beg; base < end; base += G) {
       const int e = base + (int)g.lane;
       const bool valid = e < end;
-      const int s = valid ? __ldg(C.succ + e) : 0x7fffffff;
-      const bool inr = valid && s < m;
       float4 ps = make_float4(0.f, 0.f, 0.f, 0.f);
-      float d = INF;
-      if (inr) {
-        ps = __ldg(C.pts + s);
-        d = sqd32(qx, qy, qz, ps);
-      }
+      if (valid) ps = __ldg(C.ent + e);  // site and rank of the entry
+      const int s = valid ? __float_as_int(ps.w) : 0x7fffffff;
+      const bool inr = valid && s < m;
+      const float d = inr ? sqd32(qx, qy, qz, ps) : INF;
       bool sure, maybe;
       if (dcur >= kTiny) {
         sure = inr && d < dcur * (1.f - kGuard);
@@ -285,10 +285,11 @@ __device__ __forceinline__ void knn_query(const CloudDev& C, const Grp<G>& g, fl
     for (int base = beg; base < end; base += G) {
       const int e = base + (int)g.lane;
       const bool valid = e < end;
-      const int s = valid ? __ldg(C.succ + e) : 0x7fffffff;
+      float4 ps = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (valid) ps = __ldg(C.ent + e);
+      const int s = valid ? __float_as_int(ps.w) : 0x7fffffff;
       const bool inr = valid && s < m;
-      float d = INF;
-      if (inr) d = sqd32(qx, qy, qz, __ldg(C.pts + s));
+      const float d = inr ? sqd32(qx, qy, qz, ps) : INF;
       bool pass = inr && key_lt(d, (uint32_t)s, T.kd, T.kr);
       uint32_t b = g.ballot(pass);
       while (b) {
@@ -570,11 +571,14 @@ __device__ __forceinline__ bool strictly_closer(float qx, float qy, float qz, fl
 // of the descent, or the nearest list not yet expanded). The threads of a
 // warp then advance entry by entry together whatever their row lengths,
 // instead of waiting at the end of every row for the longest one (measured
-// 1.3x-2x faster than the row-by-row loop nest). The index of the next
-// entry is loaded one iteration ahead.
+// 1.3x-2x faster than the row-by-row loop nest). Entries come from the
+// inlined table (site and rank in one 16-byte load), the next one loaded
+// one iteration ahead.
 __device__ __forceinline__ void knn_query_smem(const CloudDev& C, float qx, float qy, float qz,
                                                int k, int m, uint64_t* col,
                                                int32_t* __restrict__ oi, float* __restrict__ od) {
+  // an entry past the end of a row: rank bits 0x7fffffff, never < m
+  const float4 kNone = make_float4(0.f, 0.f, 0.f, __int_as_float(0x7fffffff));
   SmemList L;
   slist_init(L, col);
   float4 pc = __ldg(C.pts);
@@ -582,13 +586,13 @@ __device__ __forceinline__ void knn_query_smem(const CloudDev& C, float qx, floa
   slist_insert(L, pack_key(dcur, 0u), k);
   bool desc = true;
   int e = __ldg(C.rowp), end = __ldg(C.rowp + 1);
-  int s_next = e < end ? __ldg(C.succ + e) : 0x7fffffff;
+  float4 next = e < end ? __ldg(C.ent + e) : kNone;
   for (;;) {
-    if (e < end && s_next < m) {
-      const int s = s_next;
+    const int s = __float_as_int(next.w);
+    if (s < m) {  // the row's next entry exists and is in the prefix
+      const float4 ps = next;
       ++e;
-      s_next = e < end ? __ldg(C.succ + e) : 0x7fffffff;
-      const float4 ps = __ldg(C.pts + s);
+      next = e < end ? __ldg(C.ent + e) : kNone;
       const float d = sqd32(qx, qy, qz, ps);
       const uint64_t key = pack_key(d, (uint32_t)s);
       if (desc) {
@@ -598,7 +602,7 @@ __device__ __forceinline__ void knn_query_smem(const CloudDev& C, float qx, floa
           if (key < L.worst) slist_insert(L, key, k);
           e = __ldg(C.rowp + s);
           end = __ldg(C.rowp + s + 1);
-          s_next = e < end ? __ldg(C.succ + e) : 0x7fffffff;
+          next = e < end ? __ldg(C.ent + e) : kNone;
         }
       } else if (key < L.worst) {
         slist_insert(L, key, k);
@@ -615,7 +619,7 @@ __device__ __forceinline__ void knn_query_smem(const CloudDev& C, float qx, floa
     const int site = (int)(uint32_t)L.col[pos * 32];
     e = __ldg(C.rowp + site);
     end = __ldg(C.rowp + site + 1);
-    s_next = e < end ? __ldg(C.succ + e) : 0x7fffffff;
+    next = e < end ? __ldg(C.ent + e) : kNone;
   }
   for (int p = 0; p < k; ++p) {
     const bool real = p < L.cnt;

@@ -11,7 +11,12 @@ struct CloudDevHost {
   const int32_t* succ;   // [E]
   int32_t n;
   float lo[3], hi[3];    // bounding box of the sites (query sort)
+  const void* ent;       // float4[E]: succ[e]'s (x, y, z) and its rank's bits in w
 };
+
+// Fills ent[e] = (pts[succ[e]].xyz, rank bits of succ[e]) for e < E.
+cudaError_t launch_fill_entries(const void* pts, const int32_t* succ, int64_t E, void* ent,
+                                cudaStream_t stream);
 
 struct PlainLaunch {
   const float* q;

@@ -98,7 +98,7 @@ cudaError_t run_thread(const CloudDevHost& c, const PlainLaunch& L, cudaStream_t
   int64_t blocks = (int64_t)num_sms() * per_sm;
   if (need < blocks) blocks = need;
   if (blocks < 1) blocks = 1;
-  CloudDev C{(const float4*)c.pts, c.rowp, c.succ, c.n};
+  CloudDev C{(const float4*)c.pts, c.rowp, c.succ, c.n, (const float4*)c.ent};
   knn_plain_thread_kernel<K, COUNT><<<(unsigned)blocks, kThreads, 0, stream>>>(
       C, L.q, L.q_stride, L.nq, L.k, L.m, L.m_scalar, L.perm, L.out_idx, L.out_d2, L.counters,
       L.err);
@@ -179,7 +179,7 @@ cudaError_t run_smem(const CloudDevHost& c, const PlainLaunch& L, cudaStream_t s
   int64_t blocks = (int64_t)num_sms() * per_sm;
   if (need < blocks) blocks = need;
   if (blocks < 1) blocks = 1;
-  CloudDev C{(const float4*)c.pts, c.rowp, c.succ, c.n};
+  CloudDev C{(const float4*)c.pts, c.rowp, c.succ, c.n, (const float4*)c.ent};
   knn_plain_smem_kernel<THREADS><<<(unsigned)blocks, THREADS, smem, stream>>>(
       C, L.q, L.q_stride, L.nq, L.k, kcap, L.m, L.m_scalar, L.perm, L.out_idx, L.out_d2, L.err);
   return cudaGetLastError();
@@ -215,7 +215,7 @@ cudaError_t run(const CloudDevHost& c, const PlainLaunch& L, cudaStream_t stream
   int64_t blocks = (int64_t)num_sms() * per_sm;
   if (need < blocks) blocks = need;
   if (blocks < 1) blocks = 1;
-  CloudDev C{(const float4*)c.pts, c.rowp, c.succ, c.n};
+  CloudDev C{(const float4*)c.pts, c.rowp, c.succ, c.n, (const float4*)c.ent};
   knn_plain_kernel<G, S, COUNT><<<(unsigned)blocks, kThreads, 0, stream>>>(
       C, L.q, L.q_stride, L.nq, L.k, L.m, L.m_scalar, L.perm, L.out_idx, L.out_d2, L.counters,
       L.err);
@@ -270,6 +270,29 @@ int num_sms() {
 // is fastest up to k = 16 (k = 4: 359M q/s vs 264M with 8 lanes; k = 16:
 // 124M vs 111M with 16 lanes); above that the 32-slot register list costs
 // too much occupancy and 16 lanes win (k = 32: 44M vs 26M with 1 lane).
+namespace {
+
+__global__ void fill_entries_kernel(const float4* __restrict__ pts, const int32_t* __restrict__ succ,
+                                    int64_t E, float4* __restrict__ ent) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < E; e += stride) {
+    const int32_t s = __ldg(succ + e);
+    const float4 p = __ldg(pts + s);
+    ent[e] = make_float4(p.x, p.y, p.z, __int_as_float(s));
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_fill_entries(const void* pts, const int32_t* succ, int64_t E, void* ent,
+                                cudaStream_t stream) {
+  if (E <= 0) return cudaSuccess;
+  const int64_t blocks = std::min<int64_t>((E + 255) / 256, (int64_t)num_sms() * 8);
+  fill_entries_kernel<<<(unsigned)blocks, 256, 0, stream>>>((const float4*)pts, succ, E,
+                                                            (float4*)ent);
+  return cudaGetLastError();
+}
+
 int default_lanes(int k) {
   (void)k;
   return 1;

@@ -270,7 +270,7 @@ void mknn_server::launch(Slot& sl, std::vector<uint64_t>& tickets, size_t off, s
                      (const float*)(dbase + R.q_off), nullptr,
                      sorted ? (const int32_t*)(dbase + R.perm_off) : nullptr,
                      (int32_t*)(dbase + R.idx_off), (float*)(dbase + R.d2_off), c->d_err, q.k,
-                     q.m ? q.m : (int32_t)c->n};
+                     q.m ? q.m : (int32_t)c->n, (const float4*)cd.ent};
       const int v = variant_index(lanes[i], q.k);
       const int per = item_queries(lanes[i], rounds);
       if (v == kSmemVariant) kcap = std::max(kcap, (int)q.k);
