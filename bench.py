@@ -53,7 +53,7 @@ def _args():
     ap.add_argument("--no-sort", action="store_true", help="process queries in input order")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving section")
     ap.add_argument("--serve-requests", type=int, default=400)
-    ap.add_argument("--workload", default="torus", choices=["torus", "batch", "prefix"])
+    ap.add_argument("--workload", default="torus", choices=["torus", "batch", "prefix", "sites"])
     return ap.parse_args()
 
 
@@ -398,7 +398,8 @@ def prefix_workload(args, M, torch):
     for _ in range(max(3, args.warmup)):
         M.mknn_knn_ex(cloud.handle, q, nq, 3, k, m, 0, idx, d2, s, lanes=lanes)
     cnt = torch.zeros((nq, 4), dtype=torch.int32, device=dev)
-    M.mknn_knn_ex(cloud.handle, q, nq, 3, k, m, 0, idx, d2, s, lanes=lanes, counters=cnt)
+    M.mknn_knn_ex(cloud.handle, q, nq, 3, k, m, 0, idx, d2, s, counters=cnt,
+                  lanes=32 if k > 64 and lanes in (0, 1) else lanes)
     torch.cuda.synchronize()
     rows, entries, coords, trans = (int(x) for x in cnt.to(torch.int64).sum(dim=0).cpu().numpy())
     alg = 12 * nq + 4 * nq + 8 * rows + 4 * entries + 12 * coords + 8 * k * nq
@@ -429,6 +430,65 @@ def prefix_workload(args, M, torch):
     print(json.dumps(line), flush=True)
 
 
+def sites_workload(args, M, torch):
+    """Same-manifold queries: every site of the 1M-point torus queried
+    against the cloud (normal-estimation style, k = 16), and the same sites
+    probed across prefixes with k = 100 (m log-uniform in [1000, n], the
+    temporal setting of Sec. 5)."""
+    import workloads as W
+    wl = W.large_torus(n=args.n, nq=1, k=16)
+    cloud, build_s = _cloud_cache(wl.points, wl.order, f"torus{wl.n}")
+    cloud.upload()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    n = wl.n
+    sites = torch.from_numpy(W.permutation(n, 61).astype(np.int32)).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    s = stream.cuda_stream
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    out = {}
+    for k, mode in ((16, "all sites, m = n"), (100, "m log-uniform in [1000, n]")):
+        m = None
+        if k == 100:
+            u = W.uniform(62, 1, n)
+            mv = np.clip(np.floor(np.exp(np.log(1000) + u * (np.log(n) - np.log(1000)))), 1, n)
+            m = torch.from_numpy(mv.astype(np.int32)).to(dev)
+        idx = torch.empty((n, k), dtype=torch.int32, device=dev)
+        d2 = torch.empty((n, k), dtype=torch.float32, device=dev)
+        for _ in range(max(3, args.warmup)):
+            M.mknn_knn_sites(cloud.handle, sites, n, k, m, 0, idx, d2, s)
+        cnt = torch.zeros((n, 4), dtype=torch.int32, device=dev)
+        M.mknn_knn_sites(cloud.handle, sites, n, k, m, 0, idx, d2, s, counters=cnt,
+                         lanes=32 if k > 64 else 1)
+        torch.cuda.synchronize()
+        rows, entries, coords, trans = (int(x) for x in cnt.to(torch.int64).sum(dim=0).cpu().numpy())
+        alg = 4 * n + 12 * n + 8 * rows + 4 * entries + 12 * coords + 8 * k * n
+        ms = []
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            M.mknn_knn_sites(cloud.handle, sites, n, k, m, 0, idx, d2, s)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        t = float(np.mean(ms))
+        peak, kind = _peaks()
+        out[f"k{k}"] = {"workload": f"torus n={n}, {n} site queries ({mode}), k={k}",
+                        "value": n / (t / 1e3), "ms_per_step": t,
+                        "alg_bytes_per_query": alg / n,
+                        "roofline_frac": alg / (t / 1e3) / 1e9 / peak,
+                        "counts_per_query": {"rows": rows / n, "entries": entries / n,
+                                             "transitions": trans / n}}
+    line = {"metric": "same-manifold k-NN queries/sec (1M-pt torus, every site a query)",
+            "value": out["k16"]["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": True, "data": "synthetic",
+            "dtype": "f32", "config": {"l2": "flushed before every timed step",
+                                        "build_seconds": build_s if build_s is not None
+                                        else "cached"},
+            "runs": out}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = _args()
     rank, world, local = _dist_env()
@@ -445,6 +505,9 @@ def main():
         return
     if args.workload == "prefix":
         prefix_workload(args, M, torch)
+        return
+    if args.workload == "sites":
+        sites_workload(args, M, torch)
         return
     dist = None
     if world > 1:
@@ -489,8 +552,8 @@ def main():
 
     # algorithmic bytes of one launch, from the kernel's own counters (untimed)
     cnt = torch.zeros((nq, 4), dtype=torch.int32, device=dev)
-    M.mknn_knn_ex(cloud.handle, q, nq, 3, k, None, 0, idx, d2, sptr, lanes=lanes, order=order,
-                  sort=sort_flag, counters=cnt)
+    M.mknn_knn_ex(cloud.handle, q, nq, 3, k, None, 0, idx, d2, sptr, order=order,
+                  lanes=32 if k > 64 and lanes in (0, 1) else lanes, sort=sort_flag, counters=cnt)
     torch.cuda.synchronize()
     tot = cnt.to(torch.int64).sum(dim=0).cpu().numpy()
     rows, entries, coords, trans = (int(x) for x in tot)

@@ -49,7 +49,7 @@ typedef enum {
 } mknn_status;
 
 /* Largest k accepted by the query entry points. */
-#define MKNN_MAX_K 64
+#define MKNN_MAX_K 128
 
 typedef struct mknn_cloud mknn_cloud;
 
@@ -159,7 +159,9 @@ mknn_status mknn_knn(const mknn_cloud* cloud, const float* q, int64_t nq, int32_
 
 /* Tuning knobs of one query launch; zero-initialise for defaults. */
 typedef struct {
-  int32_t lanes;        /* lanes per query: 0 = default, or 1, 4, 8, 16, 32 */
+  int32_t lanes;        /* lanes per query: 0 = default, or 1, 4, 8, 16, 32
+                           (4 and 8 hold k <= 64; one lane above 64
+                           needs placement 2 and no counters) */
   int32_t sort;         /* query locality sort: 0 = default, 1 = on, -1 = off */
   int32_t blocks_per_sm;/* 0 = as many as fit */
   int32_t* counters;    /* device int32[4*nq] or NULL: per query rows opened,
@@ -197,6 +199,25 @@ size_t mknn_knn_workspace_size(int64_t nq, const mknn_knn_opts* opts);
 mknn_status mknn_knn_ex(const mknn_cloud* cloud, const float* q, int64_t nq, int32_t q_stride,
                         int32_t k, const int32_t* m, int32_t m_scalar, int32_t* out_idx,
                         float* out_d2, const mknn_knn_opts* opts, mknn_stream_t stream);
+
+/* mknn_knn_sites: same-manifold queries, where each query is one of the
+ * cloud's own sites (e.g. normal estimation, Sec. 1 and Sec. 6, or a probe
+ * at a site across prefixes, Sec. 5). Query i is the site of rank
+ * sites[i]; the rest is mknn_knn: the same Algorithms 1 and 2 with the
+ * prefix bound of Sec. 4.2, so the site itself is returned at distance 0
+ * when its rank is below m (after any earlier exact duplicate).
+ *   sites     device int32[nq] ranks in [0, n). A rank outside it yields a
+ *             padded row and sets the cloud's error flag, as a bad m does.
+ *   m, m_scalar, k, out_idx, out_d2, stream: as mknn_knn.
+ *   opts      as mknn_knn_ex (NULL for defaults), except that `order` must
+ *             be NULL (the sites are sorted by locality like queries).
+ * Scratch: 20 bytes per query (coordinates and bounds gathered from the
+ * cloud) plus mknn_knn_workspace_size; a caller workspace must hold
+ * mknn_knn_sites_workspace_size bytes. Errors: EINVAL, ENOMEM, ECUDA. */
+size_t mknn_knn_sites_workspace_size(int64_t nq, const mknn_knn_opts* opts);
+mknn_status mknn_knn_sites(const mknn_cloud* cloud, const int32_t* sites, int64_t nq, int32_t k,
+                           const int32_t* m, int32_t m_scalar, int32_t* out_idx, float* out_d2,
+                           const mknn_knn_opts* opts, mknn_stream_t stream);
 
 /* End-to-end form with HOST buffers: copies queries (and m) to the device,
  * runs the query, copies results back, in chunks pipelined over two

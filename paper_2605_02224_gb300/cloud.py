@@ -64,6 +64,19 @@ class Cloud:
             M.mknn_knn(self.handle, q, nq, int(q.stride(0)), k, m_ptr, m_scalar, idx, d2, stream)
         return idx, d2
 
+    def knn_sites(self, sites, k: int, m=None, stream: int = 0, **opt):
+        """sites: int32 CUDA tensor (nq,) of ranks; query i is that site.
+        Returns (idx int32 (nq,k), d2 float32 (nq,k))."""
+        import torch
+        nq = int(sites.shape[0])
+        idx = torch.empty((nq, k), dtype=torch.int32, device=sites.device)
+        d2 = torch.empty((nq, k), dtype=torch.float32, device=sites.device)
+        if stream == 0:
+            stream = torch.cuda.current_stream(sites.device).cuda_stream
+        m_ptr, m_scalar = (None, int(m or 0)) if (m is None or isinstance(m, int)) else (m, 0)
+        M.mknn_knn_sites(self.handle, sites, nq, k, m_ptr, m_scalar, idx, d2, stream, **opt)
+        return idx, d2
+
     def knn_host(self, q, k: int, m=None, out_idx=None, out_d2=None):
         m_arr, m_scalar = (None, int(m or 0)) if (m is None or isinstance(m, int)) else (m, 0)
         return M.mknn_knn_host(self.handle, q, k, m_arr, m_scalar, out_idx, out_d2)

@@ -37,7 +37,7 @@ namespace {
 
 constexpr int kThreads = 256;
 
-// Variants compiled into the persistent kernel: (G, S) with G*S <= 64.
+// Variants compiled into the persistent kernels: (G, S), list capacity G*S.
 struct VariantDesc {
   int g, s;
 };
@@ -45,9 +45,11 @@ struct VariantDesc {
 // (any k <= 64); the others keep a group's list in registers.
 constexpr VariantDesc kVariants[] = {{4, 1},  {4, 2},  {4, 4},  {8, 1},  {8, 2},
                                      {8, 4},  {8, 8},  {16, 1}, {16, 2}, {16, 4},
-                                     {32, 1}, {32, 2}, {1, 64}};
+                                     {32, 1}, {32, 2}, {1, 64}, {16, 8}, {32, 4},
+                                     {1, 128}};
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
-static_assert(kVariants[kSmemVariant].g == 1, "one-lane variant index");
+static_assert(kVariants[kSmemVariant].g == 1 && kVariants[kSmemVariant128].g == 1,
+              "one-lane variant indices");
 
 }  // namespace
 
@@ -69,6 +71,7 @@ __device__ __forceinline__ uint64_t* smem_column(int kcap) {
   return batch_lists + (size_t)warp * kcap * 32 + lane;
 }
 
+template <int W>
 __device__ __forceinline__ void serve_item_smem(const ReqDev& R, const Item& w, uint64_t* col) {
   const int lane = (int)(threadIdx.x & 31u);
   const CloudDev C{R.pts, R.rowp, R.succ, R.n, R.ent};
@@ -87,7 +90,7 @@ __device__ __forceinline__ void serve_item_smem(const ReqDev& R, const Item& w, 
       atomicOr(R.err, 1);
       continue;
     }
-    knn_query_smem(C, qx, qy, qz, R.k, m, col, oi, od);
+    knn_query_smem<W>(C, qx, qy, qz, R.k, m, col, oi, od);
   }
 }
 
@@ -138,7 +141,7 @@ __global__ void __launch_bounds__(kThreads) knn_batch_group_kernel(const ReqDev*
 
 // The one-lane variant: one query per thread, candidate lists in shared
 // memory, 256-thread blocks held to 48 registers as in the plain kernel.
-template <int THREADS>
+template <int THREADS, int W>
 __global__ void __launch_bounds__(THREADS, THREADS == 256 ? 5 : 1) knn_batch_smem_kernel(const ReqDev* __restrict__ reqs,
                                                                  const Item* __restrict__ items,
                                                                  int nitems,
@@ -152,7 +155,7 @@ __global__ void __launch_bounds__(THREADS, THREADS == 256 ? 5 : 1) knn_batch_sme
     it = __shfl_sync(0xffffffffu, it, 0);
     if (it >= nitems) return;
     const Item w = items[it];
-    serve_item_smem(reqs[w.req], w, col);
+    serve_item_smem<W>(reqs[w.req], w, col);
     __syncwarp();
   }
 }
@@ -223,13 +226,17 @@ std::once_flag g_attr_once;
 cudaError_t g_attr_err = cudaSuccess;
 
 void set_smem_attributes() {
-  cudaError_t e = cudaFuncSetAttribute(knn_batch_smem_kernel<256>,
+  cudaError_t e = cudaFuncSetAttribute(knn_batch_smem_kernel<256, 1>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)list_bytes(256, 32));
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(knn_batch_smem_kernel<128>,
+    e = cudaFuncSetAttribute(knn_batch_smem_kernel<128, 1>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)list_bytes(128, 64));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(knn_batch_smem_kernel<64, 2>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)list_bytes(64, 128));
   g_attr_err = e;
 }
 
@@ -248,9 +255,12 @@ const void* variant_kernel(int variant, int threads) {
     case 9: return (const void*)knn_batch_group_kernel<16, 4>;
     case 10: return (const void*)knn_batch_group_kernel<32, 1>;
     case 11: return (const void*)knn_batch_group_kernel<32, 2>;
+    case 13: return (const void*)knn_batch_group_kernel<16, 8>;
+    case 14: return (const void*)knn_batch_group_kernel<32, 4>;
     case kSmemVariant:
-      return threads == 256 ? (const void*)knn_batch_smem_kernel<256>
-                            : (const void*)knn_batch_smem_kernel<128>;
+      return threads == 256 ? (const void*)knn_batch_smem_kernel<256, 1>
+                            : (const void*)knn_batch_smem_kernel<128, 1>;
+    case kSmemVariant128: return (const void*)knn_batch_smem_kernel<64, 2>;
     default: return nullptr;
   }
 }
@@ -261,9 +271,9 @@ BatchLaunch batch_config(int nitems, int blocks_per_sm, int kcap, int variant) {
   std::call_once(g_attr_once, set_smem_attributes);
   BatchLaunch b;
   b.variant = variant;
-  const bool smem = variant == kSmemVariant;
+  const bool smem = is_smem_variant(variant);
   b.kcap = smem ? kcap : 0;
-  b.threads = smem ? (kcap <= 32 ? 256 : 128) : kThreads;
+  b.threads = variant == kSmemVariant128 ? 64 : smem ? (kcap <= 32 ? 256 : 128) : kThreads;
   b.smem = smem ? list_bytes(b.threads, kcap) : 0;
   int occ = 1;
   const void* fn = variant_kernel(variant, b.threads);
@@ -290,14 +300,17 @@ cudaError_t launch_batch_kernel(const ReqDev* d_reqs, const Item* d_items, int n
   return cudaLaunchKernel(fn, dim3((unsigned)b.grid), dim3((unsigned)b.threads), args, b.smem, s);
 }
 
-std::vector<Segment> make_segments(std::vector<Item>& items, int blocks_per_sm, int kcap) {
-  auto rank = [](int v) { return v == kSmemVariant ? -1 : v; };
+std::vector<Segment> make_segments(std::vector<Item>& items, int blocks_per_sm,
+                                   const std::vector<int>& req_k) {
+  auto rank = [](int v) { return is_smem_variant(v) ? v - 100 : v; };
   std::stable_sort(items.begin(), items.end(),
                    [&](const Item& a, const Item& c) { return rank(a.variant) < rank(c.variant); });
   std::vector<Segment> segs;
   for (int i = 0; i < (int)items.size();) {
     int j = i;
     while (j < (int)items.size() && items[j].variant == items[i].variant) ++j;
+    int kcap = 0;
+    for (int t = i; t < j; ++t) kcap = std::max(kcap, req_k[items[t].req]);
     Segment g;
     g.begin = i;
     g.count = j - i;
@@ -311,7 +324,9 @@ std::vector<Segment> make_segments(std::vector<Item>& items, int blocks_per_sm, 
 cudaError_t launch_segments(const ReqDev* d_reqs, const Item* d_items, int* d_next,
                             const std::vector<Segment>& segs, cudaStream_t s, cudaStream_t aux,
                             cudaEvent_t fork, cudaEvent_t join) {
-  const bool split = segs.size() > 1 && segs[0].launch.variant == kSmemVariant && aux;
+  bool one = false, group = false;
+  for (const Segment& g : segs) (is_smem_variant(g.launch.variant) ? one : group) = true;
+  const bool split = one && group && aux;
   cudaError_t e = cudaSuccess;
   if (split) {
     if ((e = cudaEventRecord(fork, s)) != cudaSuccess) return e;
@@ -319,7 +334,7 @@ cudaError_t launch_segments(const ReqDev* d_reqs, const Item* d_items, int* d_ne
   }
   for (size_t i = 0; i < segs.size() && e == cudaSuccess; ++i) {
     const Segment& g = segs[i];
-    cudaStream_t st = (split && i > 0) ? aux : s;
+    cudaStream_t st = (split && !is_smem_variant(g.launch.variant)) ? aux : s;
     e = launch_batch_kernel(d_reqs, d_items + g.begin, g.count, d_next + i, g.launch, st);
   }
   if (e != cudaSuccess || !split) return e;
@@ -475,15 +490,15 @@ mknn_status mknn_batch_create(const mknn_batch_req* reqs, int32_t nreq,
   for (int r = 0; r < nreq; ++r) warp_rounds += (reqs[r].nq * b->lanes[r] + 31) / 32;
   const int rounds = o.item_rounds > 0 ? o.item_rounds : auto_item_rounds(warp_rounds);
   std::vector<Item> items;
-  int kcap = 0;
+  std::vector<int> req_k(nreq);
+  for (int r = 0; r < nreq; ++r) req_k[r] = reqs[r].k;
   for (int r : orderq) {
     const int v = variant_index(b->lanes[r], reqs[r].k);
     const int per = item_queries(b->lanes[r], rounds);
-    if (v == kSmemVariant) kcap = std::max(kcap, (int)reqs[r].k);
     for (int64_t s0 = 0; s0 < reqs[r].nq; s0 += per)
       items.push_back(Item{r, (int32_t)s0, (int32_t)std::min<int64_t>(reqs[r].nq, s0 + per), v});
   }
-  b->segs = make_segments(items, o.blocks_per_sm, kcap);
+  b->segs = make_segments(items, o.blocks_per_sm, req_k);
   b->nitems = (int64_t)items.size();
   cudaError_t e;
   if ((e = cudaMalloc((void**)&b->d_reqs, sizeof(ReqDev) * std::max(nreq, 1))) != cudaSuccess ||
@@ -506,7 +521,9 @@ mknn_status mknn_batch_create(const mknn_batch_req* reqs, int32_t nreq,
     free_plan(raw);
     return bfail(MKNN_ECUDA, std::string("plan upload: ") + cudaGetErrorString(e));
   }
-  if (b->segs.size() > 1 && b->segs[0].launch.variant == kSmemVariant) {
+  bool one = false, group = false;
+  for (const Segment& g : b->segs) (is_smem_variant(g.launch.variant) ? one : group) = true;
+  if (one && group) {
     if ((e = cudaStreamCreateWithFlags(&b->aux, cudaStreamNonBlocking)) != cudaSuccess ||
         (e = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming)) != cudaSuccess ||
         (e = cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming)) != cudaSuccess) {

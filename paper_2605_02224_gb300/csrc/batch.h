@@ -42,14 +42,16 @@ inline int item_queries(int lanes, int rounds) { return (32 / lanes) * rounds; }
 // small pack is cut finer so its latency stays that of a plain launch).
 int auto_item_rounds(int64_t warp_rounds);
 
-// Variant index of the one-lane shared-memory kernel.
+// Variant indices of the one-lane shared-memory kernels (k <= 64, k <= 128).
 constexpr int kSmemVariant = 12;
+constexpr int kSmemVariant128 = 15;
+inline bool is_smem_variant(int v) { return v == kSmemVariant || v == kSmemVariant128; }
 
 // Shape of one persistent launch: one kernel variant over a queue of items.
 struct BatchLaunch {
   int grid = 1, threads = 256;
   size_t smem = 0;    // dynamic shared memory for the one-lane candidate lists
-  int kcap = 0;       // list capacity: the largest k among one-lane requests
+  int kcap = 0;       // list capacity: the largest k among the launch's requests
   int variant = kSmemVariant;
 };
 // Grid, block and shared memory for `nitems` items of one variant.
@@ -64,13 +66,16 @@ struct Segment {
   int begin = 0, count = 0;
   BatchLaunch launch;
 };
-// Reorders items by variant (the one-lane kernel's first, each variant's
-// items in their given order) and returns one segment per variant present.
-std::vector<Segment> make_segments(std::vector<Item>& items, int blocks_per_sm, int kcap);
+// Reorders items by variant (the one-lane kernels' first, each variant's
+// items in their given order) and returns one segment per variant present;
+// req_k[r] is request r's k (a one-lane segment's list capacity is its
+// largest k).
+std::vector<Segment> make_segments(std::vector<Item>& items, int blocks_per_sm,
+                                   const std::vector<int>& req_k);
 // Launches every segment, segment i draining the queue counter d_next[i]
 // (zero on entry). With one-lane and group segments both present, the
 // group segments run one after another on `aux`, forked from s and joined
-// back, concurrently with the one-lane segment on s; otherwise all run on
+// back, concurrently with the one-lane segments on s; otherwise all run on
 // s in order.
 cudaError_t launch_segments(const ReqDev* d_reqs, const Item* d_items, int* d_next,
                             const std::vector<Segment>& segs, cudaStream_t s, cudaStream_t aux,

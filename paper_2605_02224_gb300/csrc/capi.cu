@@ -112,6 +112,10 @@ constexpr int64_t kSortMinQueries = 4096;
 
 size_t perm_bytes(int64_t nq) { return ((size_t)nq * 4 + 255) & ~(size_t)255; }
 
+// Same-manifold queries: the gathered coordinates (float4) and prefix bounds.
+size_t site_q_bytes(int64_t nq) { return ((size_t)nq * 16 + 255) & ~(size_t)255; }
+size_t sites_bytes(int64_t nq) { return site_q_bytes(nq) + perm_bytes(nq); }
+
 bool sort_enabled(const mknn_knn_opts* o, int64_t nq) {
   if (o && o->sort < 0) return false;
   if (o && o->sort > 0) return true;
@@ -452,7 +456,7 @@ mknn_status mknn_knn_ex(const mknn_cloud* c, const float* q, int64_t nq, int32_t
   if (st != MKNN_OK) return st;
   if (nq < 0 || nq >= (int64_t)0x7FFFFFFF) return fail(MKNN_EINVAL, "nq out of range");
   if (q_stride < 3) return fail(MKNN_EINVAL, "q_stride must be >= 3");
-  if (k < 1 || k > MKNN_MAX_K) return fail(MKNN_EINVAL, "k must be in [1, 64]");
+  if (k < 1 || k > MKNN_MAX_K) return fail(MKNN_EINVAL, "k must be in [1, 128]");
   if (!m) {
     if (m_scalar == 0) m_scalar = (int32_t)c->n;
     if (m_scalar < 1 || m_scalar > c->n) return fail(MKNN_EINVAL, "m_scalar must be in [1, n]");
@@ -462,6 +466,10 @@ mknn_status mknn_knn_ex(const mknn_cloud* c, const float* q, int64_t nq, int32_t
   int lanes = (opts && opts->lanes) ? opts->lanes : choose_lanes(k, c->n, c->hub_bucket(), nq);
   if (lanes != 1 && lanes != 4 && lanes != 8 && lanes != 16 && lanes != 32)
     return fail(MKNN_EINVAL, "lanes must be 1, 4, 8, 16 or 32");
+  if (k > plain_max_k(lanes))
+    return fail(MKNN_EINVAL, "k above what this lane width holds (4, 8 lanes: 64; 1, 16, 32: 128)");
+  if (lanes == 1 && k > 64 && ((opts && opts->counters) || (opts && opts->placement == 1)))
+    return fail(MKNN_EINVAL, "one lane with k > 64 needs the shared-memory list (no counters)");
   cudaStream_t s = (cudaStream_t)stream;
   const int32_t* perm = opts ? opts->order : nullptr;
   if (!perm && sort_enabled(opts, nq)) {
@@ -500,6 +508,48 @@ mknn_status mknn_knn_ex(const mknn_cloud* c, const float* q, int64_t nq, int32_t
   cudaError_t e = launch_knn_plain(c->dev(), L, s);
   if (e != cudaSuccess) return cuda_fail(e, "knn kernel launch");
   return MKNN_OK;
+}
+
+size_t mknn_knn_sites_workspace_size(int64_t nq, const mknn_knn_opts* opts) {
+  if (nq <= 0) return 0;
+  return sites_bytes(nq) + mknn_knn_workspace_size(nq, opts);
+}
+
+mknn_status mknn_knn_sites(const mknn_cloud* c, const int32_t* sites, int64_t nq, int32_t k,
+                           const int32_t* m, int32_t m_scalar, int32_t* out_idx, float* out_d2,
+                           const mknn_knn_opts* opts, mknn_stream_t stream) {
+  mknn_status st = check_cloud_dev(c);
+  if (st != MKNN_OK) return st;
+  if (nq < 0 || nq >= (int64_t)0x7FFFFFFF) return fail(MKNN_EINVAL, "nq out of range");
+  if (k < 1 || k > MKNN_MAX_K) return fail(MKNN_EINVAL, "k must be in [1, 128]");
+  if (!m) {
+    if (m_scalar == 0) m_scalar = (int32_t)c->n;
+    if (m_scalar < 1 || m_scalar > c->n) return fail(MKNN_EINVAL, "m_scalar must be in [1, n]");
+  }
+  if (nq == 0) return MKNN_OK;
+  if (!sites || !out_idx || !out_d2) return fail(MKNN_EINVAL, "NULL device pointer");
+  if (opts && opts->order) return fail(MKNN_EINVAL, "order is not taken by mknn_knn_sites");
+  const size_t own = sites_bytes(nq);
+  const size_t need = mknn_knn_sites_workspace_size(nq, opts);
+  cudaStream_t s = (cudaStream_t)stream;
+  void* ws = nullptr;
+  if (opts && opts->workspace) {
+    if (opts->workspace_bytes < need)
+      return fail(MKNN_EINVAL, "workspace smaller than mknn_knn_sites_workspace_size");
+    ws = opts->workspace;
+  } else {
+    cudaError_t e = scratch_for(s, need, &ws);
+    if (e != cudaSuccess) return fail(MKNN_ENOMEM, "workspace allocation failed");
+  }
+  float4* q4 = (float4*)ws;
+  int32_t* m_eff = (int32_t*)((char*)ws + site_q_bytes(nq));
+  cudaError_t e = launch_gather_sites(c->dev(), sites, nq, m, m_scalar, q4, m_eff, s);
+  if (e != cudaSuccess) return cuda_fail(e, "site gather launch");
+  mknn_knn_opts o2{};
+  if (opts) o2 = *opts;
+  o2.workspace = (char*)ws + own;
+  o2.workspace_bytes = need - own;
+  return mknn_knn_ex(c, (const float*)q4, nq, 4, k, m_eff, 0, out_idx, out_d2, &o2, stream);
 }
 
 mknn_status mknn_knn(const mknn_cloud* c, const float* q, int64_t nq, int32_t q_stride, int32_t k,

@@ -517,22 +517,71 @@ __device__ __forceinline__ uint64_t pack_key(float d, uint32_t r) {
   return ((uint64_t)__float_as_uint(d) << 32) | r;
 }
 
+// W 64-bit words of expanded flags: W = 1 for k <= 64, 2 for k <= 128.
+template <int W>
 struct SmemList {
   uint64_t* col;   // this lane's column: col[i * 32]
   int cnt;
-  uint64_t done;   // bit i: entry at position i expanded
+  uint64_t done[W];  // bit i of the flags: entry at position i expanded
   uint64_t worst;  // key of position k-1 (a pad while cnt < k)
 };
 
-__device__ __forceinline__ void slist_init(SmemList& L, uint64_t* col) {
+template <int W>
+__device__ __forceinline__ void slist_init(SmemList<W>& L, uint64_t* col) {
   L.col = col;
   L.cnt = 0;
-  L.done = 0ull;
+#pragma unroll
+  for (int w = 0; w < W; ++w) L.done[w] = 0ull;
   L.worst = pack_key(__int_as_float(0x7f800000), kRankMask);
 }
 
+// Opens a clear flag at position pos: flags at pos and above move up one.
+__device__ __forceinline__ uint64_t flags_open(uint64_t f, int pos) {
+  const uint64_t low = pos ? (f & (~0ull >> (64 - pos))) : 0ull;
+  return low | ((f >> pos) << 1 << pos);
+}
+
+template <int W>
+__device__ __forceinline__ void flags_insert(SmemList<W>& L, int pos) {
+  if constexpr (W == 1) {
+    L.done[0] = flags_open(L.done[0], pos);
+  } else {
+    if (pos < 64) {
+      const uint64_t carry = L.done[0] >> 63;
+      L.done[0] = flags_open(L.done[0], pos);
+      L.done[1] = (L.done[1] << 1) | carry;
+    } else {
+      L.done[1] = flags_open(L.done[1], pos - 64);
+    }
+  }
+}
+
+// Position of the first entry among the first lim not yet expanded, or -1.
+template <int W>
+__device__ __forceinline__ int flags_first_clear(const SmemList<W>& L, int lim) {
+  const int l0 = min(lim, 64);
+  const uint64_t c0 = ~L.done[0] & (l0 == 64 ? ~0ull : ((1ull << l0) - 1ull));
+  if (c0) return __ffsll((long long)c0) - 1;
+  if constexpr (W == 2) {
+    if (lim > 64) {
+      const uint64_t c1 = ~L.done[1] & ((1ull << (lim - 64)) - 1ull);
+      if (c1) return 64 + __ffsll((long long)c1) - 1;
+    }
+  }
+  return -1;
+}
+
+template <int W>
+__device__ __forceinline__ void flags_set(SmemList<W>& L, int pos) {
+  if (W == 1 || pos < 64)
+    L.done[0] |= 1ull << pos;
+  else
+    L.done[W - 1] |= 1ull << (pos - 64);
+}
+
 // Inserts key c if not present; caller checks c < L.worst.
-__device__ __forceinline__ void slist_insert(SmemList& L, uint64_t c, int k) {
+template <int W>
+__device__ __forceinline__ void slist_insert(SmemList<W>& L, uint64_t c, int k) {
   int lo = 0, hi = L.cnt;
   while (lo < hi) {
     const int mid = (lo + hi) >> 1;
@@ -545,8 +594,7 @@ __device__ __forceinline__ void slist_insert(SmemList& L, uint64_t c, int k) {
   if (pos < L.cnt && L.col[pos * 32] == c) return;
   for (int i = min(L.cnt, k - 1); i > pos; --i) L.col[i * 32] = L.col[(i - 1) * 32];
   L.col[pos * 32] = c;
-  const uint64_t low = pos ? (L.done & (~0ull >> (64 - pos))) : 0ull;
-  L.done = low | ((L.done >> pos) << 1 << pos);
+  flags_insert(L, pos);
   if (L.cnt < k) L.cnt++;
   if (L.cnt == k) L.worst = L.col[(k - 1) * 32];
 }
@@ -574,12 +622,13 @@ __device__ __forceinline__ bool strictly_closer(float qx, float qy, float qz, fl
 // 1.3x-2x faster than the row-by-row loop nest). Entries come from the
 // inlined table (site and rank in one 16-byte load), the next one loaded
 // one iteration ahead.
+template <int W>
 __device__ __forceinline__ void knn_query_smem(const CloudDev& C, float qx, float qy, float qz,
                                                int k, int m, uint64_t* col,
                                                int32_t* __restrict__ oi, float* __restrict__ od) {
   // an entry past the end of a row: rank bits 0x7fffffff, never < m
   const float4 kNone = make_float4(0.f, 0.f, 0.f, __int_as_float(0x7fffffff));
-  SmemList L;
+  SmemList<W> L;
   slist_init(L, col);
   float4 pc = __ldg(C.pts);
   float dcur = sqd32(qx, qy, qz, pc);
@@ -611,11 +660,9 @@ __device__ __forceinline__ void knn_query_smem(const CloudDev& C, float qx, floa
     }
     // the current row is done: no closer site in it (descent), or fully offered
     desc = false;
-    const int lim = min(L.cnt, k - 1);
-    const uint64_t cand = ~L.done & ((1ull << lim) - 1ull);
-    if (!cand) break;
-    const int pos = __ffsll((long long)cand) - 1;
-    L.done |= 1ull << pos;
+    const int pos = flags_first_clear(L, min(L.cnt, k - 1));
+    if (pos < 0) break;
+    flags_set(L, pos);
     const int site = (int)(uint32_t)L.col[pos * 32];
     e = __ldg(C.rowp + site);
     end = __ldg(C.rowp + site + 1);

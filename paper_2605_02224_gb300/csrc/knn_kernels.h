@@ -14,6 +14,14 @@ struct CloudDevHost {
   const void* ent;       // float4[E]: succ[e]'s (x, y, z) and its rank's bits in w
 };
 
+// Same-manifold queries: q[i] = pts[sites[i]] and m_out[i] = the query's
+// prefix bound (m[i], or m_scalar when m is NULL), or 0 - which the query
+// kernels turn into a padded row and the error flag - when sites[i] is not
+// a rank of the cloud.
+cudaError_t launch_gather_sites(const CloudDevHost& c, const int32_t* sites, int64_t nq,
+                                const int32_t* m, int32_t m_scalar, float4* q, int32_t* m_out,
+                                cudaStream_t stream);
+
 // Fills ent[e] = (pts[succ[e]].xyz, rank bits of succ[e]) for e < E.
 cudaError_t launch_fill_entries(const void* pts, const int32_t* succ, int64_t E, void* ent,
                                 cudaStream_t stream);
@@ -60,6 +68,8 @@ cudaError_t launch_query_sort_split(const CloudDevHost& c, const float* q, int32
 
 int default_lanes(int k);
 int default_placement(int k);
+// Largest k the plain kernels hold with this many lanes per query.
+int plain_max_k(int lanes);
 int num_sms();
 
 }  // namespace mknn

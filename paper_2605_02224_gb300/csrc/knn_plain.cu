@@ -110,7 +110,7 @@ cudaError_t run_thread(const CloudDevHost& c, const PlainLaunch& L, cudaStream_t
 // the warp's [kcap][32] keys). 256-thread blocks are held to 48 registers
 // (five blocks per SM, no spills): left alone the compiler picks either 40
 // registers with spills or 64, both measured 5%-20% slower.
-template <int THREADS>
+template <int THREADS, int W>
 __global__ void __launch_bounds__(THREADS, THREADS == 256 ? 5 : 1) knn_plain_smem_kernel(
     CloudDev C, const float* __restrict__ q, int q_stride, int64_t nq, int k, int kcap,
     const int32_t* __restrict__ mq, int m_scalar, const int32_t* __restrict__ perm,
@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(THREADS, THREADS == 256 ? 5 : 1) knn_plain_sme
       atomicOr(err, 1);
       continue;
     }
-    knn_query_smem(C, qx, qy, qz, k, m, col, oi, od);
+    knn_query_smem<W>(C, qx, qy, qz, k, m, col, oi, od);
   }
 }
 
@@ -149,6 +149,7 @@ constexpr size_t smem_bytes(int kcap) {
 
 template <int THREADS, int KMAX>
 cudaError_t run_smem(const CloudDevHost& c, const PlainLaunch& L, cudaStream_t stream) {
+  constexpr int W = KMAX > 64 ? 2 : 1;  // words of expanded flags
   const int kcap = L.k;
   const size_t smem = smem_bytes<THREADS>(kcap);
   static std::mutex mu;
@@ -159,7 +160,7 @@ cudaError_t run_smem(const CloudDevHost& c, const PlainLaunch& L, cudaStream_t s
     std::lock_guard<std::mutex> lk(mu);
     if (!attr) {
       // once, at the largest size any k <= KMAX needs
-      cudaError_t e = cudaFuncSetAttribute(knn_plain_smem_kernel<THREADS>,
+      cudaError_t e = cudaFuncSetAttribute(knn_plain_smem_kernel<THREADS, W>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)smem_bytes<THREADS>(KMAX));
       if (e != cudaSuccess) return e;
@@ -168,7 +169,7 @@ cudaError_t run_smem(const CloudDevHost& c, const PlainLaunch& L, cudaStream_t s
     if (!occ_for[kcap]) {
       int o = 0;
       cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-          &o, knn_plain_smem_kernel<THREADS>, THREADS, smem);
+          &o, knn_plain_smem_kernel<THREADS, W>, THREADS, smem);
       if (e != cudaSuccess) return e;
       occ_for[kcap] = o < 1 ? 1 : o;
     }
@@ -180,7 +181,7 @@ cudaError_t run_smem(const CloudDevHost& c, const PlainLaunch& L, cudaStream_t s
   if (need < blocks) blocks = need;
   if (blocks < 1) blocks = 1;
   CloudDev C{(const float4*)c.pts, c.rowp, c.succ, c.n, (const float4*)c.ent};
-  knn_plain_smem_kernel<THREADS><<<(unsigned)blocks, THREADS, smem, stream>>>(
+  knn_plain_smem_kernel<THREADS, W><<<(unsigned)blocks, THREADS, smem, stream>>>(
       C, L.q, L.q_stride, L.nq, L.k, kcap, L.m, L.m_scalar, L.perm, L.out_idx, L.out_d2, L.err);
   return cudaGetLastError();
 }
@@ -189,8 +190,10 @@ template <bool COUNT>
 cudaError_t pick_thread(const CloudDevHost& c, const PlainLaunch& L, cudaStream_t stream) {
   if (!COUNT && L.placement == 2) {
     if (L.k <= 32) return run_smem<256, 32>(c, L, stream);
-    return run_smem<128, 64>(c, L, stream);
+    if (L.k <= 64) return run_smem<128, 64>(c, L, stream);
+    return run_smem<64, 128>(c, L, stream);  // 64 KB of lists per block at k = 128
   }
+  if (L.k > 64) return cudaErrorInvalidValue;  // register lists hold k <= 64
   if (L.k <= 8) return run_thread<8, COUNT>(c, L, stream);
   if (L.k <= 16) return run_thread<16, COUNT>(c, L, stream);
   if (L.k <= 32) return run_thread<32, COUNT>(c, L, stream);
@@ -227,6 +230,12 @@ cudaError_t pick_s(const CloudDevHost& c, const PlainLaunch& L, cudaStream_t str
   const int need = (L.k + G - 1) / G;
   if (need <= 1) return run<G, 1, COUNT>(c, L, stream);
   if (need <= 2) return run<G, 2, COUNT>(c, L, stream);
+  if constexpr (G == 32) {
+    if (need <= 4) return run<G, 4, COUNT>(c, L, stream);  // k <= 128
+  }
+  if constexpr (G == 16) {
+    if (need <= 8) return run<G, 8, COUNT>(c, L, stream);  // k <= 128
+  }
   if constexpr (G <= 16) {
     if (need <= 4) return run<G, 4, COUNT>(c, L, stream);
   }
@@ -282,7 +291,30 @@ __global__ void fill_entries_kernel(const float4* __restrict__ pts, const int32_
   }
 }
 
+__global__ void gather_sites_kernel(const float4* __restrict__ pts, int32_t n,
+                                    const int32_t* __restrict__ sites, int64_t nq,
+                                    const int32_t* __restrict__ m, int32_t m_scalar,
+                                    float4* __restrict__ q, int32_t* __restrict__ m_out) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nq; i += stride) {
+    const int32_t r = __ldg(sites + i);
+    const bool ok = r >= 0 && r < n;
+    q[i] = ok ? __ldg(pts + r) : make_float4(0.f, 0.f, 0.f, 0.f);
+    m_out[i] = ok ? (m ? __ldg(m + i) : m_scalar) : 0;
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_gather_sites(const CloudDevHost& c, const int32_t* sites, int64_t nq,
+                                const int32_t* m, int32_t m_scalar, float4* q, int32_t* m_out,
+                                cudaStream_t stream) {
+  if (nq <= 0) return cudaSuccess;
+  const int64_t blocks = std::min<int64_t>((nq + 255) / 256, (int64_t)num_sms() * 8);
+  gather_sites_kernel<<<(unsigned)blocks, 256, 0, stream>>>((const float4*)c.pts, c.n, sites, nq,
+                                                            m, m_scalar, q, m_out);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_fill_entries(const void* pts, const int32_t* succ, int64_t E, void* ent,
                                 cudaStream_t stream) {
@@ -302,6 +334,8 @@ int default_lanes(int k) {
 // fastest variant measured at every k (1M-site torus, 4M box queries:
 // k=4 449M q/s, k=16 168M, k=32 60M, k=64 14M; registers: 368M, 125M,
 // 26M, 3M; best group of lanes: 264M, 111M, 44M, 13M).
+int plain_max_k(int lanes) { return (lanes == 4 || lanes == 8) ? 64 : 128; }
+
 int default_placement(int k) {
   (void)k;
   return 2;

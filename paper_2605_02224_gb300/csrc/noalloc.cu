@@ -97,7 +97,7 @@ extern "C" mknn_status mknn_knn_noalloc(const mknn_cloud* c, const float* q, int
     return MKNN_EINVAL;
   }
   if (k < 1 || k > MKNN_MAX_K) {
-    set_error("k must be in [1, 64]");
+    set_error("k must be in [1, 128]");
     return MKNN_EINVAL;
   }
   if (!m) {
@@ -139,6 +139,7 @@ extern "C" mknn_status mknn_knn_noalloc(const mknn_cloud* c, const float* q, int
   L.counters = nullptr;
   L.err = c->d_err;
   L.lanes = default_lanes(k);
+  L.placement = default_placement(k);
   L.blocks_per_sm = 0;
   if ((e = launch_knn_plain(cd, L, s)) != cudaSuccess) {
     set_error(std::string("knn kernel launch: ") + cudaGetErrorString(e));

@@ -237,7 +237,7 @@ void mknn_server::launch(Slot& sl, std::vector<uint64_t>& tickets, size_t off, s
     const int nreq = (int)tickets.size();
     std::vector<ReqDev> rd(nreq);
     std::vector<Item> items;
-    int kcap = 0;
+    std::vector<int> req_k(nreq);
     int64_t pack_nq = 0;  // the pack runs as one launch per variant: its size sets the lanes
     for (int i = 0; i < nreq; ++i) pack_nq += recs[tickets[i] - 1].r.nq;
     std::vector<int> lanes(nreq);
@@ -273,11 +273,11 @@ void mknn_server::launch(Slot& sl, std::vector<uint64_t>& tickets, size_t off, s
                      q.m ? q.m : (int32_t)c->n, (const float4*)cd.ent};
       const int v = variant_index(lanes[i], q.k);
       const int per = item_queries(lanes[i], rounds);
-      if (v == kSmemVariant) kcap = std::max(kcap, (int)q.k);
+      req_k[i] = q.k;
       for (int64_t b0 = 0; b0 < q.nq; b0 += per)
         items.push_back(Item{i, (int32_t)b0, (int32_t)std::min<int64_t>(q.nq, b0 + per), v});
     }
-    const std::vector<Segment> segs = make_segments(items, 0, kcap);
+    const std::vector<Segment> segs = make_segments(items, 0, req_k);
     const size_t ni = items.size();
     const size_t items_off = reqs_off + al(sizeof(ReqDev) * nreq);
     // request table and items go through the pinned mirror

@@ -17,7 +17,7 @@ _LIB_PATH = os.path.join(_HERE, "libmknn.so")
 
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "EBUSY", 5: "ETIMEOUT",
           6: "EDEGENERATE", 7: "EIO"}
-MKNN_MAX_K = 64
+MKNN_MAX_K = 128
 
 
 class MknnError(RuntimeError):
@@ -118,6 +118,8 @@ def _declare(L):
         "mknn_knn_workspace_size": (sz, [i64, vp]),
         "mknn_knn_ex": (i32, [vp, vp, i64, i32, i32, vp, i32, vp, vp, vp, vp]),
         "mknn_knn_host": (i32, [vp, vp, i64, i32, i32, vp, i32, vp, vp, vp]),
+        "mknn_knn_sites": (i32, [vp, vp, i64, i32, vp, i32, vp, vp, vp, vp]),
+        "mknn_knn_sites_workspace_size": (C.c_size_t, [i64, vp]),
         "mknn_cloud_check": (i32, [vp, vp]),
         "mknn_query_order_workspace_size": (sz, [i64]),
         "mknn_query_order": (i32, [vp, vp, i64, i32, vp, vp, sz, vp]),
@@ -290,6 +292,20 @@ def mknn_knn_ex(cloud: int, q, nq: int, q_stride: int, k: int, m, m_scalar: int,
     o = _opts(**opt)
     _check(lib().mknn_knn_ex(cloud, _ptr(q), nq, q_stride, k, _ptr(m), m_scalar, _ptr(out_idx),
                              _ptr(out_d2), C.addressof(o), stream or None))
+
+
+def mknn_knn_sites(cloud: int, sites, nq: int, k: int, m, m_scalar: int, out_idx, out_d2,
+                   stream: int = 0, **opt):
+    """Same-manifold queries: query i is the cloud's site of rank sites[i]
+    (device int32)."""
+    o = _opts(**opt)
+    _check(lib().mknn_knn_sites(cloud, _ptr(sites), nq, k, _ptr(m), m_scalar, _ptr(out_idx),
+                                _ptr(out_d2), C.addressof(o), stream or None))
+
+
+def mknn_knn_sites_workspace_size(nq: int, **opt) -> int:
+    o = _opts(**opt)
+    return int(lib().mknn_knn_sites_workspace_size(nq, C.addressof(o)))
 
 
 def mknn_knn_host(cloud: int, q, k: int, m=None, m_scalar: int = 0, out_idx=None, out_d2=None,

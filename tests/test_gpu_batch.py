@@ -110,6 +110,42 @@ def test_plan_with_many_variants_equals_plain(torch, clouds, tmp_path):
         M.mknn_tune_clear()
 
 
+def test_large_k_requests_in_a_plan(torch, clouds):
+    """Requests with k = 65, 100 and 128 (the one-lane kernel with 128-slot
+    lists, or 16 and 32 lanes) mixed with the workload's own: the plan equals
+    plain launches, and a sample equals the oracle."""
+    reqs, keep = _requests(torch, clouds[:3], "array")
+    for (wl, c), k in zip(clouds[3:6], (65, 100, 128)):
+        q = torch.from_numpy(wl.queries).cuda()
+        idx = torch.full((wl.nq, k), -9, dtype=torch.int32, device="cuda")
+        d2 = torch.full((wl.nq, k), -9.0, dtype=torch.float32, device="cuda")
+        reqs.append(dict(cloud=c.handle, q=q, nq=wl.nq, q_stride=3, k=k, m=None, m_scalar=0,
+                         out_idx=idx, out_d2=d2))
+        keep.append((wl, c, q, None, 0, idx, d2, k))
+    for forced in (0, 32, 16):
+        plan = M.mknn_batch_create(reqs, lanes=forced)
+        lanes, _, _ = M.mknn_batch_info(plan, len(reqs))
+        assert all(l in (1, 16, 32) for l in lanes[3:])
+        M.mknn_batch_run(plan, torch.cuda.current_stream().cuda_stream)
+        torch.cuda.synchronize()
+        M.mknn_batch_free(plan)
+        _check_large_k(torch, keep)
+
+
+def _check_large_k(torch, keep):
+    for item in keep:
+        wl, c, q, m, ms, idx, d2 = item[:7]
+        k = item[7] if len(item) > 7 else wl.k
+        pi, pd = _plain(torch, c, q, k, m, ms)
+        assert np.array_equal(idx.cpu().numpy(), pi), wl.name
+        assert np.array_equal(d2.cpu().numpy(), pd), wl.name
+        if k > 64:
+            parity.check_rows(wl.ranked_points(), wl.queries, k, 0, idx.cpu().numpy(),
+                              d2.cpu().numpy(), rows=range(0, wl.nq, max(1, wl.nq // 60)))
+        idx.fill_(-9)
+        d2.fill_(-9.0)
+
+
 def test_batch_against_oracle_sample(torch, clouds):
     reqs, keep = _requests(torch, clouds, "array")
     plan = M.mknn_batch_create(reqs)
@@ -177,6 +213,6 @@ def test_batch_rejects_bad_requests(torch, clouds):
     with pytest.raises(M.MknnError) as ei:
         M.mknn_batch_create(reqs)
     assert ei.value.status == 1
-    reqs[1]["k"] = 65
+    reqs[1]["k"] = 129
     with pytest.raises(M.MknnError):
         M.mknn_batch_create(reqs)

@@ -45,9 +45,14 @@ def test_tiny_exhaustive(n, table):
         c = Cloud.build(P, order).upload()
     Q = W.box_queries(60, 7, [-1.5] * 3, [1.5] * 3)
     Q = np.concatenate([Q, Pr[: min(n, 20)]])          # queries exactly on sites
-    ks = sorted({1, 2, min(n, 8), min(n + 1, 64), 33, 64})
+    ks = sorted({1, 2, min(n, 8), min(n + 1, 64), 33, 64, 100, 128})
     for v in VARIANTS:
         for k in ks:
+            small = v["lanes"] in (4, 8) or (v["lanes"] == 1 and v["placement"] == 1)
+            if k > 64 and small:                       # these variants hold k <= 64
+                with pytest.raises(M.MknnError):
+                    run_knn(c, Q, k, **v)
+                continue
             for m in sorted({1, max(1, n // 2), n}):
                 idx, d2 = run_knn(c, Q, k, m, **v, sort=1 if k % 2 else -1)
                 parity.check_rows(Pr, Q, k, m, idx, d2)
@@ -159,6 +164,33 @@ def test_hub_rows_all_variants():
     c.close()
 
 
+def test_large_k_with_prefix_bounds():
+    """k above 64 (the temporal-defect setting of Sec. 5 uses k = 100):
+    near-surface and volume queries with per-query m on a 20,000-site bumpy
+    sphere, one lane (shared-memory list), 16 and 32 lanes and the default
+    bit-identical, rows against the oracle."""
+    P, _ = W.bumpy_sphere(20000, 31)
+    order = W.permutation(20000, 32)
+    c = built_cloud(P, order, "bumpy20k")
+    c.upload()
+    Pr = P[order]
+    nq = 1200
+    Q = np.concatenate([W.box_queries(nq // 2, 41, [-1.3] * 3, [1.3] * 3),
+                        W.near_surface_queries("bumpy", nq - nq // 2, 42)])
+    m = np.clip(np.floor(np.exp(W.uniform(43, 1, nq) * np.log(20000))), 1, 20000).astype(np.int32)
+    for k in (65, 100, 128):
+        base = None
+        for lanes in (0, 1, 16, 32):
+            idx, d2 = run_knn(c, Q, k, m, lanes=lanes)
+            if base is None:
+                parity.check_row_properties(idx, d2, k, m.astype(np.int64), 20000)
+                parity.check_rows(Pr, Q, k, m, idx, d2, rows=range(0, nq, 3))
+                base = (idx, d2)
+            else:
+                assert np.array_equal(idx, base[0]) and np.array_equal(d2, base[1]), (k, lanes)
+    c.close()
+
+
 def test_invalid_per_query_m_sets_flag_and_pads():
     import torch
     wl = W.small_sphere(nq=64)
@@ -174,7 +206,7 @@ def test_invalid_per_query_m_sets_flag_and_pads():
     parity.check_rows(wl.ranked_points(), wl.queries, 8, m, idx, d2,
                       rows=[i for i in range(64) if i not in (5, 9)])
     with pytest.raises(M.MknnError):
-        c.knn(torch.zeros((4, 3), device="cuda"), 65)
+        c.knn(torch.zeros((4, 3), device="cuda"), 129)
     with pytest.raises(M.MknnError):
         c.knn(torch.zeros((4, 3), device="cuda"), 8, 2001)
     idx, d2 = c.knn(torch.zeros((0, 3), device="cuda"), 8)
