@@ -73,7 +73,10 @@ const char* mknn_last_error(void);
  * outputs (builds of several clouds may run in parallel threads). */
 typedef struct {
   int32_t keep_tets; /* nonzero: keep the final tetrahedra (mknn_cloud_tets) */
-  int32_t reserved[7];
+  int32_t dynamic;   /* nonzero: keep the triangulation so that points can be
+                        appended later (mknn_cloud_append); the points must
+                        span 3D (EDEGENERATE otherwise) */
+  int32_t reserved[6];
 } mknn_build_opts;
 
 mknn_status mknn_build(const float* xyz, int64_t n, const int64_t* order,
@@ -96,8 +99,32 @@ mknn_status mknn_cloud_from_table(const float* xyz_ranked, int64_t n, const int6
  * entries with each entry's site inlined (float4 x, y, z, rank), which the
  * query kernels read with one load per entry. Idempotent; synchronous with
  * respect to the host (the copies complete before return). Device bytes:
- * 16 n + 4 (n+1) + 20 E plus a few words of status. Errors: ENOMEM, ECUDA. */
+ * 24 n + 20 E plus a few words of status (a dynamic cloud also reserves
+ * room for appends: a quarter more sites and entries, at least 4096 sites
+ * and 65536 entries). Errors: ENOMEM, ECUDA. */
 mknn_status mknn_cloud_upload(mknn_cloud* cloud, mknn_stream_t stream);
+
+/* mknn_cloud_append: inserts `count` new points after the existing ones,
+ * in the given order (their birth times follow every existing point:
+ * ranks n, n+1, ..., input indices n, n+1, ... for mknn_cloud_order). The
+ * cloud must have been built with mknn_build_opts.dynamic. The insertion
+ * continues the build's triangulation (Sec. 3), so the table afterwards is
+ * the one a build over all the points in this order would make: every
+ * existing list gains the new ranks whose insertion made them Delaunay
+ * neighbours, and each new rank starts an empty list. Queries with m <= the
+ * old n therefore see exactly the old cloud (Sec. 4.2).
+ *   xyz    host float32[count*3].
+ *   stream used for the device update when the cloud is uploaded.
+ * On the device only the changed rows move: a row that outgrows its room is
+ * copied to the top of an append-only entry arena, which (like the site
+ * arrays) grows by reallocation when full. The call synchronises the
+ * stream. Queries on other streams must not overlap it, batch plans made
+ * before it must be recreated (mknn_batch_run returns EINVAL), and a cloud
+ * held by a server cannot be appended to (EBUSY).
+ * Errors: EINVAL (not dynamic, NULL, non-finite coordinate, n would exceed
+ * 2^31 - 16), EBUSY, ENOMEM, ECUDA. */
+mknn_status mknn_cloud_append(mknn_cloud* cloud, const float* xyz, int64_t count,
+                              mknn_stream_t stream);
 
 /* Releases device memory of the cloud (keeps the host copy). */
 mknn_status mknn_cloud_release_device(mknn_cloud* cloud);
@@ -299,7 +326,8 @@ typedef struct mknn_batch mknn_batch;
 mknn_status mknn_batch_create(const mknn_batch_req* reqs, int32_t nreq,
                               const mknn_batch_opts* opts, mknn_batch** out);
 /* Enqueues one run of the plan on the stream (asynchronous). Runs of one
- * plan must not overlap on the device (they share the queue counter). */
+ * plan must not overlap on the device (they share the queue counter).
+ * EINVAL if a request's cloud was appended to after the plan was made. */
 mknn_status mknn_batch_run(mknn_batch* plan, mknn_stream_t stream);
 /* Lanes chosen per request (int32[nreq], may be NULL), work items, and the
  * blocks of the plan's persistent launches (one launch per kernel variant

@@ -14,8 +14,8 @@ class Cloud:
         self.n, self.E, _ = M.mknn_cloud_info(handle)
 
     @classmethod
-    def build(cls, xyz, order=None, keep_tets: bool = False) -> "Cloud":
-        return cls(M.mknn_build(xyz, order, keep_tets))
+    def build(cls, xyz, order=None, keep_tets: bool = False, dynamic: bool = False) -> "Cloud":
+        return cls(M.mknn_build(xyz, order, keep_tets, dynamic))
 
     @classmethod
     def from_table(cls, xyz_ranked, rowp, succ) -> "Cloud":
@@ -27,6 +27,11 @@ class Cloud:
 
     def save(self, path: str):
         M.mknn_cloud_save(self.handle, path)
+
+    def append(self, xyz, stream: int = 0) -> "Cloud":
+        """Inserts points after the existing ones (dynamic clouds)."""
+        M.mknn_cloud_append(self.handle, xyz, stream)
+        return self
 
     def upload(self, stream: int = 0) -> "Cloud":
         M.mknn_cloud_upload(self.handle, stream)

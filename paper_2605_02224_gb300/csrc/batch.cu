@@ -74,7 +74,7 @@ __device__ __forceinline__ uint64_t* smem_column(int kcap) {
 template <int W>
 __device__ __forceinline__ void serve_item_smem(const ReqDev& R, const Item& w, uint64_t* col) {
   const int lane = (int)(threadIdx.x & 31u);
-  const CloudDev C{R.pts, R.rowp, R.succ, R.n, R.ent};
+  const CloudDev C{R.pts, R.rows, R.succ, R.n, R.ent};
   for (int i = w.begin + lane; i < w.end; i += 32) {
     const int64_t qi = R.perm ? (int64_t)__ldg(R.perm + i) : (int64_t)i;
     const float* qp = R.q + qi * R.q_stride;
@@ -99,7 +99,7 @@ __device__ __forceinline__ void serve_item(const ReqDev& R, const Item& w) {
   const Grp<G> g;
   const int gi = (int)((threadIdx.x & 31u) / G);
   constexpr int kGroups = 32 / G;
-  const CloudDev C{R.pts, R.rowp, R.succ, R.n, R.ent};
+  const CloudDev C{R.pts, R.rows, R.succ, R.n, R.ent};
   for (int i = w.begin + gi; i < w.end; i += kGroups) {
     const int64_t qi = R.perm ? (int64_t)__ldg(R.perm + i) : (int64_t)i;
     const float* qp = R.q + qi * R.q_stride;
@@ -361,6 +361,7 @@ struct mknn_batch {
   int device = -1;
   int nreq = 0;
   std::vector<mknn_batch_req> reqs;
+  std::vector<uint64_t> gens;    // each request's cloud generation when the plan was made
   std::vector<int> lanes;        // chosen lanes per request
   ReqDev* d_reqs = nullptr;
   // work items grouped by kernel variant, one queue counter per segment
@@ -437,6 +438,8 @@ mknn_status mknn_batch_create(const mknn_batch_req* reqs, int32_t nreq,
   b->device = dev;
   b->nreq = nreq;
   b->reqs.assign(reqs, reqs + nreq);
+  b->gens.resize(nreq);
+  for (int r = 0; r < nreq; ++r) b->gens[r] = reqs[r].cloud ? reqs[r].cloud->generation.load() : 0;
   b->lanes.resize(nreq);
   b->cell_off.assign(nreq, 0);
   b->perm_off.assign(nreq, 0);
@@ -465,7 +468,7 @@ mknn_status mknn_batch_create(const mknn_batch_req* reqs, int32_t nreq,
       return bfail(MKNN_EINVAL, "request " + std::to_string(r) + ": lanes/k combination");
     b->lanes[r] = lanes;
     const CloudDevHost cd = R.cloud->dev();
-    rd[r] = ReqDev{(const float4*)cd.pts, cd.rowp,   cd.succ, cd.n,  R.q_stride,
+    rd[r] = ReqDev{(const float4*)cd.pts, cd.rows,   cd.succ, cd.n,  R.q_stride,
                    R.q,                   R.m,       nullptr, R.out_idx,
                    R.out_d2,              R.cloud->d_err, R.k, ms, (const float4*)cd.ent};
     cost[r] = (double)R.k * std::log2((double)R.cloud->n + 2.0);
@@ -564,6 +567,10 @@ mknn_status mknn_batch_run(mknn_batch* b, mknn_stream_t stream) {
   int dev = -1;
   cudaGetDevice(&dev);
   if (dev != b->device) return bfail(MKNN_EINVAL, "plan was made on another device");
+  for (int r = 0; r < b->nreq; ++r)
+    if (b->reqs[r].cloud && b->reqs[r].cloud->generation.load() != b->gens[r])
+      return bfail(MKNN_EINVAL, "request " + std::to_string(r) +
+                                    ": its cloud changed (append) since the plan was made");
   cudaError_t e = b->exec ? cudaGraphLaunch(b->exec, (cudaStream_t)stream)
                           : enqueue(b, (cudaStream_t)stream);
   if (e != cudaSuccess) return bfail(MKNN_ECUDA, std::string("batch run: ") + cudaGetErrorString(e));

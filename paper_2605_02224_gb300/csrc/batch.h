@@ -11,7 +11,7 @@ namespace mknn {
 // One request as the persistent kernel sees it (device-side copy).
 struct ReqDev {
   const float4* pts;
-  const int32_t* rowp;
+  const int2* rows;
   const int32_t* succ;
   int32_t n;
   int32_t q_stride;

@@ -47,7 +47,7 @@
 
 namespace mknn {
 
-namespace {
+namespace build_detail {
 
 constexpr int32_t INF = -1;
 constexpr int32_t DEAD = -2;
@@ -67,6 +67,11 @@ struct Lists {
     tail.assign(n, -1);
     len.assign(n, 0);
     pool.reserve((size_t)n + 16);
+  }
+  void grow(int64_t n) {  // rows for new ranks, empty
+    head.resize(n, -1);
+    tail.resize(n, -1);
+    len.resize(n, 0);
   }
   void append(int32_t i, int32_t j) {
     int32_t t = tail[i];
@@ -101,8 +106,20 @@ class Builder {
   Builder(const float* xyz, int64_t n) : X_(xyz), n_((int32_t)n) {}
 
   bool run(bool keep_tets, SuccessorTable* out, std::string* err);
+  // Inserts ranks n_ .. n_new-1 of xyz (the same points below n_); each
+  // successor entry added is reported as (row, rank) in `added`.
+  bool append(const float* xyz, int32_t n_new, std::vector<std::pair<int32_t, int32_t>>* added,
+              std::string* err);
+  void csr(std::vector<int64_t>* rowp, std::vector<int32_t>* succ) const;
+  int32_t size() const { return n_; }
+  bool has_tetrahedron() const { return tet_made_; }
+  const BuildStats& stats() const { return st_; }
 
  private:
+  // One rank after the degenerate prefix: descent to its nearest earlier
+  // site over the lists so far, then insertion (or a duplicate's entry).
+  // Returns false on a location failure.
+  bool insert_rank(int32_t j, std::string* err);
   const float* P(int32_t v) const { return X_ + 3 * (int64_t)v; }
   bool is_inf(int32_t t) const {
     const int32_t* v = &V_[4 * (size_t)t];
@@ -151,6 +168,8 @@ class Builder {
 
   const float* X_;
   int32_t n_;
+  bool tet_made_ = false;
+  std::vector<std::pair<int32_t, int32_t>>* added_ = nullptr;
   std::vector<int32_t> V_, N_;
   std::vector<uint32_t> mark_;
   std::vector<int32_t> free_;
@@ -360,10 +379,98 @@ int Builder::insert(int32_t j, int32_t start, bool record) {
       int32_t v = f.v[q];
       if (v == INF || vstamp_[v] == (uint32_t)j + 1) continue;
       vstamp_[v] = (uint32_t)j + 1;
-      if (record) L_.append(v, j);
+      if (record) {
+        L_.append(v, j);
+        if (added_) added_->push_back({v, j});
+      }
     }
   }
   return 0;
+}
+
+bool Builder::insert_rank(int32_t j, std::string* err) {
+  const float* p = P(j);
+  int32_t curr = 0;
+  double dc = dist2(p, P(0));
+restart:
+  for (int32_t bk = L_.head[curr]; bk >= 0; bk = L_.pool[bk].next) {
+    const Lists::Block& B = L_.pool[bk];
+    for (int q = 0; q < B.cnt; ++q) {
+      int32_t s = B.e[q];
+      double ds = dist2(p, P(s));
+      if (ds < dc) {
+        curr = s;
+        dc = ds;
+        goto restart;
+      }
+    }
+  }
+  if (dc == 0.0) {
+    twin_[j] = twin_[curr];
+    L_.append(curr, j);
+    if (added_) added_->push_back({curr, j});
+    st_.duplicates++;
+    return true;
+  }
+  int32_t start = vtet_[twin_[curr]];
+  int rc = insert(j, start, true);
+  if (rc < 0) {
+    *err = "point location failed at rank " + std::to_string(j);
+    return false;
+  }
+  if (rc == 1) {
+    L_.append(twin_[j], j);
+    if (added_) added_->push_back({twin_[j], j});
+    st_.duplicates++;
+  }
+  return true;
+}
+
+void Builder::csr(std::vector<int64_t>* rowp, std::vector<int32_t>* succ) const {
+  const int32_t n = n_;
+  rowp->assign((size_t)n + 1, 0);
+  for (int32_t i = 0; i < n; ++i) (*rowp)[i + 1] = (*rowp)[i] + L_.len[i];
+  succ->resize((size_t)(*rowp)[n]);
+  for (int32_t i = 0; i < n; ++i) {
+    int64_t o = (*rowp)[i];
+    for (int32_t bk = L_.head[i]; bk >= 0; bk = L_.pool[bk].next)
+      for (int q = 0; q < L_.pool[bk].cnt; ++q) (*succ)[o++] = L_.pool[bk].e[q];
+  }
+}
+
+bool Builder::append(const float* xyz, int32_t n_new,
+                     std::vector<std::pair<int32_t, int32_t>>* added, std::string* err) {
+  if (!tet_made_) {
+    *err = "appending needs a cloud whose first points span 3D (not all coplanar)";
+    return false;
+  }
+  if (n_new < n_) {
+    *err = "append cannot remove points";
+    return false;
+  }
+  for (int64_t i = 3 * (int64_t)n_; i < 3 * (int64_t)n_new; ++i) {
+    if (!std::isfinite(xyz[i])) {
+      *err = "non-finite coordinate at rank " + std::to_string(i / 3);
+      return false;
+    }
+  }
+  X_ = xyz;
+  const int32_t n_old = n_;
+  n_ = n_new;
+  L_.grow(n_new);
+  vtet_.resize(n_new, -1);
+  vstamp_.resize(n_new, 0);
+  twin_.resize(n_new);
+  for (int32_t i = n_old; i < n_new; ++i) twin_[i] = i;
+  added_ = added;
+  bool ok = true;
+  for (int32_t j = n_old; j < n_new && ok; ++j) ok = insert_rank(j, err);
+  added_ = nullptr;
+  st_.n = n_;
+  int64_t e = 0;
+  for (int32_t i = 0; i < n_; ++i) e += L_.len[i];
+  st_.entries = e;
+  return ok;
 }
 
 bool Builder::run(bool keep_tets, SuccessorTable* out, std::string* err) {
@@ -415,50 +522,12 @@ bool Builder::run(bool keep_tets, SuccessorTable* out, std::string* err) {
       }
       if (rc == 1) st_.duplicates++;
     }
-    for (int32_t j = j0 + 1; j < n; ++j) {
-      const float* p = P(j);
-      int32_t curr = 0;
-      double dc = dist2(p, P(0));
-    restart:
-      for (int32_t bk = L_.head[curr]; bk >= 0; bk = L_.pool[bk].next) {
-        const Lists::Block& B = L_.pool[bk];
-        for (int q = 0; q < B.cnt; ++q) {
-          int32_t s = B.e[q];
-          double ds = dist2(p, P(s));
-          if (ds < dc) {
-            curr = s;
-            dc = ds;
-            goto restart;
-          }
-        }
-      }
-      if (dc == 0.0) {
-        twin_[j] = twin_[curr];
-        L_.append(curr, j);
-        st_.duplicates++;
-        continue;
-      }
-      int32_t start = vtet_[twin_[curr]];
-      int rc = insert(j, start, true);
-      if (rc < 0) {
-        *err = "point location failed at rank " + std::to_string(j);
-        return false;
-      }
-      if (rc == 1) {
-        L_.append(twin_[j], j);
-        st_.duplicates++;
-      }
-    }
+    tet_made_ = true;
+    for (int32_t j = j0 + 1; j < n; ++j)
+      if (!insert_rank(j, err)) return false;
   }
 
-  out->rowp.assign((size_t)n + 1, 0);
-  for (int32_t i = 0; i < n; ++i) out->rowp[i + 1] = out->rowp[i] + L_.len[i];
-  out->succ.resize((size_t)out->rowp[n]);
-  for (int32_t i = 0; i < n; ++i) {
-    int64_t o = out->rowp[i];
-    for (int32_t bk = L_.head[i]; bk >= 0; bk = L_.pool[bk].next)
-      for (int q = 0; q < L_.pool[bk].cnt; ++q) out->succ[o++] = L_.pool[bk].e[q];
-  }
+  csr(&out->rowp, &out->succ);
   int64_t finite = 0;
   const int32_t ntets = (int32_t)(V_.size() / 4);
   out->tets.clear();
@@ -480,7 +549,7 @@ bool Builder::run(bool keep_tets, SuccessorTable* out, std::string* err) {
   return true;
 }
 
-}  // namespace
+}  // namespace build_detail
 
 bool build_successor_table(const float* xyz, int64_t n, bool keep_tets, SuccessorTable* out,
                            std::string* err) {
@@ -489,12 +558,63 @@ bool build_successor_table(const float* xyz, int64_t n, bool keep_tets, Successo
     return false;
   }
   try {
-    Builder b(xyz, n);
+    build_detail::Builder b(xyz, n);
     return b.run(keep_tets, out, err);
   } catch (const std::bad_alloc&) {
     *err = "out of host memory while building";
     return false;
   }
 }
+
+IncrementalTable::IncrementalTable() = default;
+IncrementalTable::~IncrementalTable() = default;
+
+bool IncrementalTable::build(const float* xyz, int64_t n, bool keep_tets, SuccessorTable* out,
+                             std::string* err) {
+  if (n < 0 || n > (int64_t)0x7FFFFFF0) {
+    *err = "n out of range";
+    return false;
+  }
+  try {
+    b_.reset(new build_detail::Builder(xyz, n));
+    if (!b_->run(keep_tets, out, err)) {
+      b_.reset();
+      return false;
+    }
+    return true;
+  } catch (const std::bad_alloc&) {
+    b_.reset();
+    *err = "out of host memory while building";
+    return false;
+  }
+}
+
+bool IncrementalTable::append(const float* xyz, int64_t n_new,
+                              std::vector<std::pair<int32_t, int32_t>>* added, std::string* err) {
+  if (!b_) {
+    *err = "no triangulation kept";
+    return false;
+  }
+  if (n_new > (int64_t)0x7FFFFFF0) {
+    *err = "n out of range";
+    return false;
+  }
+  try {
+    return b_->append(xyz, (int32_t)n_new, added, err);
+  } catch (const std::bad_alloc&) {
+    *err = "out of host memory while appending";
+    return false;
+  }
+}
+
+void IncrementalTable::csr(std::vector<int64_t>* rowp, std::vector<int32_t>* succ) const {
+  if (b_) b_->csr(rowp, succ);
+}
+
+int64_t IncrementalTable::size() const { return b_ ? b_->size() : 0; }
+
+bool IncrementalTable::can_append() const { return b_ && b_->has_tetrahedron(); }
+
+BuildStats IncrementalTable::stats() const { return b_ ? b_->stats() : BuildStats{}; }
 
 }  // namespace mknn

@@ -7,6 +7,7 @@
 // therefore ascending. Ranks are 0-based.
 #pragma once
 #include <cstdint>
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -40,5 +41,33 @@ bool build_successor_table(const float* xyz, int64_t n, bool keep_tets,
 
 // Largest all-coplanar input for which a complete table is produced.
 constexpr int64_t kMaxCoplanarComplete = 4096;
+
+namespace build_detail {
+class Builder;
+}
+
+// A successor table that keeps its triangulation, so that points can be
+// appended later (ranks n, n+1, ... in append order). Appending continues
+// the same insertion, so the lists equal those of one build over all the
+// points; an appended rank j only adds entries j to existing lists
+// (Delaunay neighbours of p_j in DT(P_{1:j})) and starts its own empty.
+class IncrementalTable {
+ public:
+  IncrementalTable();
+  ~IncrementalTable();
+  bool build(const float* xyz, int64_t n, bool keep_tets, SuccessorTable* out, std::string* err);
+  // xyz holds n_new points in rank order whose first size() are the points
+  // already inserted; inserts the others. Each successor entry added is
+  // reported as (row, rank) in `added`, in insertion order.
+  bool append(const float* xyz, int64_t n_new, std::vector<std::pair<int32_t, int32_t>>* added,
+              std::string* err);
+  void csr(std::vector<int64_t>* rowp, std::vector<int32_t>* succ) const;
+  int64_t size() const;
+  bool can_append() const;  // false when the points so far are all coplanar
+  BuildStats stats() const;
+
+ private:
+  std::unique_ptr<build_detail::Builder> b_;
+};
 
 }  // namespace mknn

@@ -57,7 +57,7 @@ void free_device(mknn_cloud* c) {
     cudaGetDevice(&cur);
     cudaSetDevice(c->device);
     cudaFree(c->d_pts);
-    cudaFree(c->d_rowp);
+    cudaFree(c->d_rows);
     cudaFree(c->d_succ);
     cudaFree(c->d_ent);
     cudaFree(c->d_err);
@@ -65,7 +65,11 @@ void free_device(mknn_cloud* c) {
   }
   c->d_pts = nullptr;
   c->d_ent = nullptr;
-  c->d_rowp = c->d_succ = c->d_err = nullptr;
+  c->pts_cap = c->ent_cap = c->ent_top = 0;
+  c->row_first.clear();
+  c->row_cap.clear();
+  c->d_rows = nullptr;
+  c->d_succ = c->d_err = nullptr;
   c->device = -1;
   c->dev_bytes = 0;
 }
@@ -180,7 +184,18 @@ mknn_status mknn_build(const float* xyz, int64_t n, const int64_t* order,
     SuccessorTable t;
     std::string err;
     const bool keep = opts && opts->keep_tets;
-    if (!build_successor_table(c->xyz.data(), n, keep, &t, &err)) {
+    bool ok;
+    if (opts && opts->dynamic) {
+      c->inc.reset(new IncrementalTable());
+      ok = c->inc->build(c->xyz.data(), n, keep, &t, &err);
+      if (ok && !c->inc->can_append()) {
+        ok = false;
+        err = "a dynamic cloud needs points that span 3D (these are all coplanar)";
+      }
+    } else {
+      ok = build_successor_table(c->xyz.data(), n, keep, &t, &err);
+    }
+    if (!ok) {
       const bool degen = err.find("coplanar") != std::string::npos;
       const bool oom = err.find("memory") != std::string::npos;
       return fail(degen ? MKNN_EDEGENERATE : (oom ? MKNN_ENOMEM : MKNN_EINVAL), err);
@@ -250,11 +265,20 @@ mknn_status mknn_cloud_upload(mknn_cloud* c, mknn_stream_t stream) {
   if (c->d_pts && c->device == cur) return MKNN_OK;
   if (c->d_pts) free_device(c);
   const int64_t n = c->n, E = c->E();
+  // a dynamic cloud gets headroom for appended sites and entries
+  const bool dyn = (bool)c->inc;
+  const int64_t pcap = dyn ? n + std::max<int64_t>(n / 4, 4096) : n;
+  const int64_t ecap = std::max<int64_t>(dyn ? E + std::max<int64_t>(E / 4, 1 << 16) : E, 1);
+  if (ecap >= (int64_t)0x7FFFFFFF) return fail(MKNN_EINVAL, "entry arena exceeds 2^31 entries");
   std::vector<float> p4;
-  std::vector<int32_t> rp32;
+  std::vector<int2> rows;
   try {
     p4.resize(4 * n);
-    rp32.resize(n + 1);
+    rows.resize(n);
+    if (dyn) {
+      c->row_first.resize(n);
+      c->row_cap.resize(n);
+    }
   } catch (const std::bad_alloc&) {
     return fail(MKNN_ENOMEM, "host allocation failed");
   }
@@ -263,14 +287,17 @@ mknn_status mknn_cloud_upload(mknn_cloud* c, mknn_stream_t stream) {
     p4[4 * i + 1] = c->xyz[3 * i + 1];
     p4[4 * i + 2] = c->xyz[3 * i + 2];
     p4[4 * i + 3] = 0.f;
+    rows[i] = make_int2((int32_t)c->rowp[i], (int32_t)c->rowp[i + 1]);
+    if (dyn) {
+      c->row_first[i] = c->rowp[i];
+      c->row_cap[i] = c->rowp[i + 1] - c->rowp[i];
+    }
   }
-  for (int64_t i = 0; i <= n; ++i) rp32[i] = (int32_t)c->rowp[i];
   c->device = cur;
-  const size_t b_pts = (size_t)n * 16, b_rowp = (size_t)(n + 1) * 4,
-               b_succ = (size_t)std::max<int64_t>(E, 1) * 4,
-               b_ent = (size_t)std::max<int64_t>(E, 1) * 16;
+  const size_t b_pts = (size_t)pcap * 16, b_rows = (size_t)pcap * 8, b_succ = (size_t)ecap * 4,
+               b_ent = (size_t)ecap * 16;
   if ((e = cudaMalloc(&c->d_pts, b_pts)) != cudaSuccess ||
-      (e = cudaMalloc((void**)&c->d_rowp, b_rowp)) != cudaSuccess ||
+      (e = cudaMalloc((void**)&c->d_rows, b_rows)) != cudaSuccess ||
       (e = cudaMalloc((void**)&c->d_succ, b_succ)) != cudaSuccess ||
       (e = cudaMalloc(&c->d_ent, b_ent)) != cudaSuccess ||
       (e = cudaMalloc((void**)&c->d_err, 256)) != cudaSuccess) {
@@ -279,8 +306,9 @@ mknn_status mknn_cloud_upload(mknn_cloud* c, mknn_stream_t stream) {
     return fail(MKNN_ENOMEM, std::string("device allocation failed: ") + cudaGetErrorString(e));
   }
   cudaStream_t s = (cudaStream_t)stream;
-  if ((e = cudaMemcpyAsync(c->d_pts, p4.data(), b_pts, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
-      (e = cudaMemcpyAsync(c->d_rowp, rp32.data(), b_rowp, cudaMemcpyHostToDevice, s)) !=
+  if ((e = cudaMemcpyAsync(c->d_pts, p4.data(), (size_t)n * 16, cudaMemcpyHostToDevice, s)) !=
+          cudaSuccess ||
+      (e = cudaMemcpyAsync(c->d_rows, rows.data(), (size_t)n * 8, cudaMemcpyHostToDevice, s)) !=
           cudaSuccess ||
       (E > 0 && (e = cudaMemcpyAsync(c->d_succ, c->succ.data(), (size_t)E * 4,
                                      cudaMemcpyHostToDevice, s)) != cudaSuccess) ||
@@ -290,7 +318,10 @@ mknn_status mknn_cloud_upload(mknn_cloud* c, mknn_stream_t stream) {
     free_device(c);
     return cuda_fail(e, "upload");
   }
-  c->dev_bytes = b_pts + b_rowp + b_succ + b_ent + 256;
+  c->pts_cap = pcap;
+  c->ent_cap = ecap;
+  c->ent_top = E;
+  c->dev_bytes = b_pts + b_rows + b_succ + b_ent + 256;
   return MKNN_OK;
 }
 

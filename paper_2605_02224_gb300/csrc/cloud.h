@@ -7,6 +7,8 @@
 #include <string>
 #include <vector>
 
+#include <memory>
+
 #include "builder.h"
 #include "knn_kernels.h"
 
@@ -19,14 +21,24 @@ struct mknn_cloud {
   std::vector<int32_t> tets;     // optional, 4 per finite tetrahedron
   mknn::BuildStats stats;
   float lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+  // kept triangulation of a cloud built with the dynamic option (appends)
+  std::unique_ptr<mknn::IncrementalTable> inc;
+  // bumped by every append: plans made before it refuse to run
+  std::atomic<uint64_t> generation{0};
   // device copy
   int device = -1;
   void* d_pts = nullptr;         // float4[n]
-  int32_t* d_rowp = nullptr;     // [n+1]
+  int2* d_rows = nullptr;        // [n]: (first, end) of each row in d_succ / d_ent
   int32_t* d_succ = nullptr;     // [E]
   void* d_ent = nullptr;         // float4[E]: succ with the sites' coordinates inlined
   int32_t* d_err = nullptr;      // error flags
   size_t dev_bytes = 0;
+  // device capacities: sites (d_pts, d_rows) and entries (d_succ, d_ent);
+  // a dynamic cloud's rows live in an append-only arena: row i occupies
+  // [row_first[i], row_first[i] + its length) with room up to row_cap[i],
+  // and a row that outgrows its room moves to the arena's top
+  int64_t pts_cap = 0, ent_cap = 0, ent_top = 0;
+  std::vector<int64_t> row_first, row_cap;
   std::atomic<int> holders{0};   // servers referencing the cloud
   mutable std::mutex mu;
 
@@ -47,7 +59,7 @@ struct mknn_cloud {
   mknn::CloudDevHost dev() const {
     mknn::CloudDevHost c;
     c.pts = d_pts;
-    c.rowp = d_rowp;
+    c.rows = d_rows;
     c.succ = d_succ;
     c.ent = d_ent;
     c.n = (int32_t)n;

@@ -43,7 +43,7 @@ constexpr float kTiny = 1e-30f;
 
 struct CloudDev {
   const float4* __restrict__ pts;
-  const int32_t* __restrict__ rowp;
+  const int2* __restrict__ rows;     // (first, end) of each successor row
   const int32_t* __restrict__ succ;
   int32_t n;
   // succ with each entry's site inlined: (x, y, z, rank bits), one 16-byte
@@ -198,8 +198,8 @@ __device__ __forceinline__ void knn_query(const CloudDev& C, const Grp<G>& g, fl
     qc.trans = 1;
   }
   for (;;) {
-    const int beg = __ldg(C.rowp + curr);
-    const int end = __ldg(C.rowp + curr + 1);
+    const int2 rr = __ldg(C.rows + curr);
+    const int beg = rr.x, end = rr.y;
     if (COUNT) qc.rows++;
     bool moved = false;
     for (int base = beg; base < end; base += G) {
@@ -279,8 +279,8 @@ __device__ __forceinline__ void knn_query(const CloudDev& C, const Grp<G>& g, fl
       for (int s = 0; s < S; ++s)
         if (s == psl) T.r[s] |= kDoneBit;
     }
-    const int beg = __ldg(C.rowp + site);
-    const int end = __ldg(C.rowp + site + 1);
+    const int2 rr = __ldg(C.rows + site);
+    const int beg = rr.x, end = rr.y;
     if (COUNT) qc.rows++;
     for (int base = beg; base < end; base += G) {
       const int e = base + (int)g.lane;
@@ -417,8 +417,9 @@ __device__ __forceinline__ void knn_query_thread(const CloudDev& C, float qx, fl
     qc.trans = 1;
   }
   for (;;) {
-    int e = __ldg(C.rowp + curr);
-    const int end = __ldg(C.rowp + curr + 1);
+    const int2 rr = __ldg(C.rows + curr);
+    int e = rr.x;
+    const int end = rr.y;
     if (COUNT) qc.rows++;
     bool moved = false;
     for (; e < end; ++e) {
@@ -470,8 +471,9 @@ __device__ __forceinline__ void knn_query_thread(const CloudDev& C, float qx, fl
     for (int i = 0; i < K; ++i)
       if (i == bi) T.r[i] |= kDoneBit;
     const int site = (int)br;
-    int e = __ldg(C.rowp + site);
-    const int end = __ldg(C.rowp + site + 1);
+    const int2 rr = __ldg(C.rows + site);
+    int e = rr.x;
+    const int end = rr.y;
     if (COUNT) qc.rows++;
     for (; e < end; ++e) {
       const int s = __ldg(C.succ + e);
@@ -634,7 +636,8 @@ __device__ __forceinline__ void knn_query_smem(const CloudDev& C, float qx, floa
   float dcur = sqd32(qx, qy, qz, pc);
   slist_insert(L, pack_key(dcur, 0u), k);
   bool desc = true;
-  int e = __ldg(C.rowp), end = __ldg(C.rowp + 1);
+  int2 rr = __ldg(C.rows);
+  int e = rr.x, end = rr.y;
   float4 next = e < end ? __ldg(C.ent + e) : kNone;
   for (;;) {
     const int s = __float_as_int(next.w);
@@ -649,8 +652,9 @@ __device__ __forceinline__ void knn_query_smem(const CloudDev& C, float qx, floa
           dcur = d;
           pc = ps;
           if (key < L.worst) slist_insert(L, key, k);
-          e = __ldg(C.rowp + s);
-          end = __ldg(C.rowp + s + 1);
+          rr = __ldg(C.rows + s);
+          e = rr.x;
+          end = rr.y;
           next = e < end ? __ldg(C.ent + e) : kNone;
         }
       } else if (key < L.worst) {
@@ -664,8 +668,9 @@ __device__ __forceinline__ void knn_query_smem(const CloudDev& C, float qx, floa
     if (pos < 0) break;
     flags_set(L, pos);
     const int site = (int)(uint32_t)L.col[pos * 32];
-    e = __ldg(C.rowp + site);
-    end = __ldg(C.rowp + site + 1);
+    rr = __ldg(C.rows + site);
+    e = rr.x;
+    end = rr.y;
     next = e < end ? __ldg(C.ent + e) : kNone;
   }
   for (int p = 0; p < k; ++p) {

@@ -7,7 +7,7 @@ namespace mknn {
 
 struct CloudDevHost {
   const void* pts;       // float4[n]
-  const int32_t* rowp;   // [n+1]
+  const int2* rows;      // [n]: (first, end) of each successor row in succ / ent
   const int32_t* succ;   // [E]
   int32_t n;
   float lo[3], hi[3];    // bounding box of the sites (query sort)

@@ -98,7 +98,7 @@ cudaError_t run_thread(const CloudDevHost& c, const PlainLaunch& L, cudaStream_t
   int64_t blocks = (int64_t)num_sms() * per_sm;
   if (need < blocks) blocks = need;
   if (blocks < 1) blocks = 1;
-  CloudDev C{(const float4*)c.pts, c.rowp, c.succ, c.n, (const float4*)c.ent};
+  CloudDev C{(const float4*)c.pts, c.rows, c.succ, c.n, (const float4*)c.ent};
   knn_plain_thread_kernel<K, COUNT><<<(unsigned)blocks, kThreads, 0, stream>>>(
       C, L.q, L.q_stride, L.nq, L.k, L.m, L.m_scalar, L.perm, L.out_idx, L.out_d2, L.counters,
       L.err);
@@ -180,7 +180,7 @@ cudaError_t run_smem(const CloudDevHost& c, const PlainLaunch& L, cudaStream_t s
   int64_t blocks = (int64_t)num_sms() * per_sm;
   if (need < blocks) blocks = need;
   if (blocks < 1) blocks = 1;
-  CloudDev C{(const float4*)c.pts, c.rowp, c.succ, c.n, (const float4*)c.ent};
+  CloudDev C{(const float4*)c.pts, c.rows, c.succ, c.n, (const float4*)c.ent};
   knn_plain_smem_kernel<THREADS, W><<<(unsigned)blocks, THREADS, smem, stream>>>(
       C, L.q, L.q_stride, L.nq, L.k, kcap, L.m, L.m_scalar, L.perm, L.out_idx, L.out_d2, L.err);
   return cudaGetLastError();
@@ -218,7 +218,7 @@ cudaError_t run(const CloudDevHost& c, const PlainLaunch& L, cudaStream_t stream
   int64_t blocks = (int64_t)num_sms() * per_sm;
   if (need < blocks) blocks = need;
   if (blocks < 1) blocks = 1;
-  CloudDev C{(const float4*)c.pts, c.rowp, c.succ, c.n, (const float4*)c.ent};
+  CloudDev C{(const float4*)c.pts, c.rows, c.succ, c.n, (const float4*)c.ent};
   knn_plain_kernel<G, S, COUNT><<<(unsigned)blocks, kThreads, 0, stream>>>(
       C, L.q, L.q_stride, L.nq, L.k, L.m, L.m_scalar, L.perm, L.out_idx, L.out_d2, L.counters,
       L.err);

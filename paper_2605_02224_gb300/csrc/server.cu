@@ -266,7 +266,7 @@ void mknn_server::launch(Slot& sl, std::vector<uint64_t>& tickets, size_t off, s
         e = launch_query_sort_split(cd, (const float*)(dbase + R.q_off), 3, q.nq, d_hist,
                                     (int32_t*)(dbase + R.cell_off), (int32_t*)(dbase + R.perm_off),
                                     s);
-      rd[i] = ReqDev{(const float4*)cd.pts, cd.rowp, cd.succ, cd.n, 3,
+      rd[i] = ReqDev{(const float4*)cd.pts, cd.rows, cd.succ, cd.n, 3,
                      (const float*)(dbase + R.q_off), nullptr,
                      sorted ? (const int32_t*)(dbase + R.perm_off) : nullptr,
                      (int32_t*)(dbase + R.idx_off), (float*)(dbase + R.d2_off), c->d_err, q.k,

@@ -27,7 +27,7 @@ class MknnError(RuntimeError):
 
 
 class mknn_build_opts(C.Structure):
-    _fields_ = [("keep_tets", C.c_int32), ("reserved", C.c_int32 * 7)]
+    _fields_ = [("keep_tets", C.c_int32), ("dynamic", C.c_int32), ("reserved", C.c_int32 * 6)]
 
 
 class mknn_build_stats(C.Structure):
@@ -119,6 +119,7 @@ def _declare(L):
         "mknn_knn_ex": (i32, [vp, vp, i64, i32, i32, vp, i32, vp, vp, vp, vp]),
         "mknn_knn_host": (i32, [vp, vp, i64, i32, i32, vp, i32, vp, vp, vp]),
         "mknn_knn_sites": (i32, [vp, vp, i64, i32, vp, i32, vp, vp, vp, vp]),
+        "mknn_cloud_append": (i32, [vp, vp, i64, vp]),
         "mknn_knn_sites_workspace_size": (C.c_size_t, [i64, vp]),
         "mknn_cloud_check": (i32, [vp, vp]),
         "mknn_query_order_workspace_size": (sz, [i64]),
@@ -177,14 +178,21 @@ def _host(a, dtype):
 
 # ---------------------------------------------------------------- build / cloud
 
-def mknn_build(xyz, order=None, keep_tets: bool = False) -> int:
+def mknn_build(xyz, order=None, keep_tets: bool = False, dynamic: bool = False) -> int:
     """Builds the successor table on the host; returns the cloud handle."""
     x = _host(xyz, np.float32).reshape(-1, 3)
     o = None if order is None else _host(order, np.int64)
-    opts = mknn_build_opts(keep_tets=1 if keep_tets else 0)
+    opts = mknn_build_opts(keep_tets=1 if keep_tets else 0, dynamic=1 if dynamic else 0)
     out = C.c_void_p()
     _check(lib().mknn_build(_ptr(x), x.shape[0], _ptr(o), C.addressof(opts), C.byref(out)))
     return out.value
+
+
+def mknn_cloud_append(cloud: int, xyz, stream: int = 0):
+    """Appends points (host float32 (count, 3), in birth order) to a cloud
+    built with dynamic=True."""
+    x = _host(xyz, np.float32).reshape(-1, 3)
+    _check(lib().mknn_cloud_append(cloud, _ptr(x), x.shape[0], stream or None))
 
 
 def mknn_cloud_from_table(xyz_ranked, rowp, succ) -> int:

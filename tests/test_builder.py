@@ -277,3 +277,86 @@ def test_sphere_small_workload_queries_exact():
         rb, _ = ok.knn_one(Pr, q, wl.k, Pr.shape[0])
         assert list(r) == list(rb)
     M.mknn_cloud_free(h)
+
+
+# ------------------------------------------------------------- appends
+
+def _ranked(P, order):
+    return np.ascontiguousarray(P[order], np.float32)
+
+
+@pytest.mark.parametrize("kind,n,n0", [("sphere", 3000, 500), ("patches", 2500, 40),
+                                       ("torus", 4000, 3999)])
+def test_appends_equal_one_build(kind, n, n0):
+    """Build the first n0 ranks with the dynamic option, append the rest in
+    chunks of 1, 7, 100 and the remainder: the table equals one build over
+    all the points in the same order, entry for entry."""
+    from paper_2605_02224_gb300 import Cloud
+    P, _ = W.surface(kind, n, 71)
+    Pr = _ranked(P, W.permutation(n, 72))
+    ref = Cloud.build(Pr)
+    c = Cloud.build(Pr[:n0], dynamic=True)
+    at = n0
+    for step in (1, 7, 100, n):
+        if at >= n:
+            break
+        c.append(Pr[at:at + step])
+        at = min(n, at + step)
+    x1, r1, s1 = c.table()
+    x2, r2, s2 = ref.table()
+    assert np.array_equal(x1, x2) and np.array_equal(r1, r2) and np.array_equal(s1, s2)
+    assert np.array_equal(c.order(), np.arange(n))
+    st = c.stats()
+    assert st["n"] == n and st["entries"] == s2.size
+    c.close()
+    ref.close()
+
+
+def test_appends_with_duplicates_match_the_definition():
+    """Appended points that repeat earlier ones (and each other): the table
+    equals one build, and every row holds the definition's list (Delaunay
+    neighbours at insertion, computed by the oracle)."""
+    from paper_2605_02224_gb300 import Cloud
+    P, _ = W.uniform_cube(60, 81)
+    extra = np.concatenate([P[:5], P[:2], W.uniform_cube(20, 82)[0]]).astype(np.float32)
+    allp = np.concatenate([P, extra]).astype(np.float32)
+    c = Cloud.build(P, dynamic=True)
+    c.append(extra[:3])
+    c.append(extra[3:])
+    ref = Cloud.build(allp)
+    t1, t2 = c.table(), ref.table()
+    assert all(np.array_equal(a, b) for a, b in zip(t1, t2))
+    rowp, succ = t1[1], t1[2]
+    # coincident points: either twin may stand for both in the library's
+    # triangulation, so read its neighbours through the earlier twin
+    first = {}
+    twin = [first.setdefault(tuple(p), r) for r, p in enumerate(allp.tolist())]
+    defn = osucc.successor_lists(allp)
+    for i, lst in enumerate(defn):
+        row = set(succ[rowp[twin[i]]:rowp[twin[i] + 1]].tolist())
+        assert set(lst) <= row, i
+    c.close()
+    ref.close()
+
+
+def test_append_errors_leave_the_cloud_unchanged():
+    from paper_2605_02224_gb300 import Cloud
+    P, _ = W.sphere(500, 91)
+    static = Cloud.build(P)
+    with pytest.raises(M.MknnError) as ei:
+        static.append(P[:3])
+    assert ei.value.status == 1                        # EINVAL: not dynamic
+    c = Cloud.build(P, dynamic=True)
+    bad = np.array([[0.1, 0.2, np.nan]], np.float32)
+    with pytest.raises(M.MknnError):
+        c.append(bad)
+    assert M.mknn_cloud_info(c.handle)[0] == 500
+    c.append(np.zeros((0, 3), np.float32))              # nothing to do
+    assert M.mknn_cloud_info(c.handle)[0] == 500
+    flat = np.stack([W.uniform(92, 1, 50), W.uniform(92, 2, 50),
+                     np.zeros(50)], 1).astype(np.float32)
+    with pytest.raises(M.MknnError) as ei:
+        Cloud.build(flat, dynamic=True)
+    assert ei.value.status == 6                        # EDEGENERATE: coplanar
+    static.close()
+    c.close()
