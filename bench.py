@@ -53,7 +53,10 @@ def _args():
     ap.add_argument("--no-sort", action="store_true", help="process queries in input order")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving section")
     ap.add_argument("--serve-requests", type=int, default=400)
-    ap.add_argument("--workload", default="torus", choices=["torus", "batch", "prefix", "sites"])
+    ap.add_argument("--workload", default="torus",
+                    choices=["torus", "batch", "prefix", "sites", "dynamic"])
+    ap.add_argument("--append-batch", type=int, default=10000,
+                    help="dynamic workload: points per append call")
     return ap.parse_args()
 
 
@@ -489,6 +492,72 @@ def sites_workload(args, M, torch):
     print(json.dumps(line), flush=True)
 
 
+def dynamic_workload(args, M, torch):
+    """Dynamic insertion: the 1M-point torus built over its first 90% of
+    ranks with the dynamic option and uploaded, then the last 10% appended
+    in batches (host insertion + device update, timed per call); queries
+    afterwards against one static build over all the points (same rows,
+    same speed expected)."""
+    import workloads as W
+    from paper_2605_02224_gb300 import Cloud
+    wl = W.large_torus(n=args.n, nq=args.nq, k=args.k)
+    Pr = np.ascontiguousarray(wl.ranked_points(), np.float32)
+    n = wl.n
+    n0 = n - n // 10
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream(dev)
+    s = stream.cuda_stream
+    t0 = time.perf_counter()
+    c = Cloud.build(Pr[:n0], dynamic=True)
+    build_s = time.perf_counter() - t0
+    c.upload(s)
+    ms = []
+    B = max(1, args.append_batch)
+    for at in range(n0, n, B):
+        t1 = time.perf_counter()
+        c.append(Pr[at:min(n, at + B)], s)
+        ms.append((time.perf_counter() - t1) * 1e3)
+    appended = n - n0
+    static, _ = _cloud_cache(wl.points, wl.order, f"torus{wl.n}")
+    static.upload(s)
+    q = torch.from_numpy(wl.queries).to(dev)
+    k, nq = wl.k, wl.nq
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+
+    def timed(cl):
+        idx = torch.empty((nq, k), dtype=torch.int32, device=dev)
+        d2 = torch.empty((nq, k), dtype=torch.float32, device=dev)
+        for _ in range(max(3, args.warmup)):
+            M.mknn_knn(cl.handle, q, nq, 3, k, None, 0, idx, d2, s)
+        out = []
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            M.mknn_knn(cl.handle, q, nq, 3, k, None, 0, idx, d2, s)
+            b.record(stream)
+            torch.cuda.synchronize()
+            out.append(a.elapsed_time(b))
+        return float(np.mean(out)), idx, d2
+
+    t_dyn, i1, d1 = timed(c)
+    t_sta, i2, d2 = timed(static)
+    same = bool(torch.equal(i1, i2) and torch.equal(d1, d2))
+    line = {"metric": "appended points/sec (dynamic 1M-pt torus, host insertion + device update)",
+            "value": appended / (sum(ms) / 1e3), "unit": "points/s", "n_gpus": 1,
+            "higher_is_better": True, "data": "synthetic", "dtype": "f32",
+            "config": {"workload": f"torus n={n}: {n0} built (dynamic), {appended} appended in "
+                                   f"batches of {B}; {nq} volume queries, k={k}",
+                       "build_seconds_dynamic": build_s},
+            "append_ms_per_call": {"mean": float(np.mean(ms)), "p50": float(np.median(ms)),
+                                   "max": float(np.max(ms)), "calls": len(ms)},
+            "queries_after_appends": {"value": nq / (t_dyn / 1e3), "ms_per_step": t_dyn},
+            "queries_static_build": {"value": nq / (t_sta / 1e3), "ms_per_step": t_sta},
+            "results_identical": same,
+            "device_bytes": {"dynamic": c.device_bytes(), "static": static.device_bytes()}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = _args()
     rank, world, local = _dist_env()
@@ -508,6 +577,9 @@ def main():
         return
     if args.workload == "sites":
         sites_workload(args, M, torch)
+        return
+    if args.workload == "dynamic":
+        dynamic_workload(args, M, torch)
         return
     dist = None
     if world > 1:
