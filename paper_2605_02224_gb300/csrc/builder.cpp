@@ -112,6 +112,18 @@ class Builder {
               std::string* err);
   void csr(std::vector<int64_t>* rowp, std::vector<int32_t>* succ) const;
   int32_t size() const { return n_; }
+  int64_t row_len(int32_t i) const { return L_.len[i]; }
+  int64_t longest_row() const {
+    int64_t mx = 0;
+    for (int32_t i = 0; i < n_; ++i) mx = std::max<int64_t>(mx, L_.len[i]);
+    return mx;
+  }
+  void row_tail(int32_t i, int64_t from, std::vector<int32_t>* out) const {
+    int64_t at = 0;
+    for (int32_t bk = L_.head[i]; bk >= 0; bk = L_.pool[bk].next)
+      for (int q = 0; q < L_.pool[bk].cnt; ++q, ++at)
+        if (at >= from) out->push_back(L_.pool[bk].e[q]);
+  }
   bool has_tetrahedron() const { return tet_made_; }
   const BuildStats& stats() const { return st_; }
 
@@ -612,6 +624,16 @@ void IncrementalTable::csr(std::vector<int64_t>* rowp, std::vector<int32_t>* suc
 }
 
 int64_t IncrementalTable::size() const { return b_ ? b_->size() : 0; }
+
+int64_t IncrementalTable::entries() const { return b_ ? b_->stats().entries : 0; }
+
+int64_t IncrementalTable::row_len(int32_t i) const { return b_ ? b_->row_len(i) : 0; }
+
+int64_t IncrementalTable::longest_row() const { return b_ ? b_->longest_row() : 0; }
+
+void IncrementalTable::row_tail(int32_t i, int64_t from, std::vector<int32_t>* out) const {
+  if (b_) b_->row_tail(i, from, out);
+}
 
 bool IncrementalTable::can_append() const { return b_ && b_->has_tetrahedron(); }
 

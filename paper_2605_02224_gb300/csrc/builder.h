@@ -63,6 +63,11 @@ class IncrementalTable {
               std::string* err);
   void csr(std::vector<int64_t>* rowp, std::vector<int32_t>* succ) const;
   int64_t size() const;
+  int64_t entries() const;
+  int64_t row_len(int32_t i) const;
+  int64_t longest_row() const;
+  // Appends entries [from, row_len(i)) of row i to *out.
+  void row_tail(int32_t i, int64_t from, std::vector<int32_t>* out) const;
   bool can_append() const;  // false when the points so far are all coplanar
   BuildStats stats() const;
 

@@ -264,6 +264,7 @@ mknn_status mknn_cloud_upload(mknn_cloud* c, mknn_stream_t stream) {
   if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
   if (c->d_pts && c->device == cur) return MKNN_OK;
   if (c->d_pts) free_device(c);
+  c->sync_csr();
   const int64_t n = c->n, E = c->E();
   // a dynamic cloud gets headroom for appended sites and entries
   const bool dyn = (bool)c->inc;
@@ -359,6 +360,7 @@ mknn_status mknn_cloud_table(const mknn_cloud* c, float* xyz_ranked, int64_t* ro
                              int32_t* succ) {
   if (!c) return fail(MKNN_EINVAL, "cloud is NULL");
   if (xyz_ranked) std::memcpy(xyz_ranked, c->xyz.data(), c->xyz.size() * 4);
+  c->sync_csr();
   if (rowp) std::memcpy(rowp, c->rowp.data(), c->rowp.size() * 8);
   if (succ) std::memcpy(succ, c->succ.data(), c->succ.size() * 4);
   return MKNN_OK;
@@ -397,6 +399,7 @@ mknn_status mknn_cloud_save(const mknn_cloud* c, const char* path) {
   if (!c || !path) return fail(MKNN_EINVAL, "NULL argument");
   FILE* f = std::fopen(path, "wb");
   if (!f) return fail(MKNN_EIO, std::string("cannot open ") + path);
+  c->sync_csr();
   const int64_t hdr[4] = {1, c->n, c->E(), 0};
   bool ok = std::fwrite(kMagic, 1, 8, f) == 8 && std::fwrite(hdr, 8, 4, f) == 4 &&
             std::fwrite(c->lo, 4, 3, f) == 3 && std::fwrite(c->hi, 4, 3, f) == 3 &&

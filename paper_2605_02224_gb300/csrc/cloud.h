@@ -16,8 +16,12 @@ struct mknn_cloud {
   int64_t n = 0;
   std::vector<float> xyz;        // 3n, rank order
   std::vector<int64_t> order;    // rank -> input index
-  std::vector<int64_t> rowp;     // n+1
-  std::vector<int32_t> succ;     // E
+  // the table as CSR; for a dynamic cloud the builder's lists are the
+  // truth and this copy is refreshed on demand after appends (sync_csr)
+  mutable std::vector<int64_t> rowp;  // n+1
+  mutable std::vector<int32_t> succ;  // E
+  mutable std::atomic<bool> csr_stale{false};
+  mutable std::mutex csr_mu;
   std::vector<int32_t> tets;     // optional, 4 per finite tetrahedron
   mknn::BuildStats stats;
   float lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
@@ -42,14 +46,24 @@ struct mknn_cloud {
   std::atomic<int> holders{0};   // servers referencing the cloud
   mutable std::mutex mu;
 
-  int64_t E() const { return (int64_t)succ.size(); }
+  int64_t E() const { return inc ? inc->entries() : (int64_t)succ.size(); }
+  void sync_csr() const {
+    if (!csr_stale.load()) return;
+    std::lock_guard<std::mutex> lk(csr_mu);
+    if (!csr_stale.load()) return;
+    inc->csr(&rowp, &succ);
+    csr_stale.store(false);
+  }
   // floor(log2(1 + longest successor list)): the tuning table's cloud shape
   // key (hub rows make queries costly whatever the size)
   int hub_bucket() const {
     int hb = hub_.load(std::memory_order_relaxed);
     if (hb >= 0) return hb;
     int64_t mx = 0;
-    for (size_t i = 0; i + 1 < rowp.size(); ++i) mx = std::max<int64_t>(mx, rowp[i + 1] - rowp[i]);
+    if (inc)
+      mx = inc->longest_row();
+    else
+      for (size_t i = 0; i + 1 < rowp.size(); ++i) mx = std::max<int64_t>(mx, rowp[i + 1] - rowp[i]);
     hb = 0;
     while ((int64_t(2) << hb) <= mx + 1) ++hb;
     hub_.store(hb, std::memory_order_relaxed);

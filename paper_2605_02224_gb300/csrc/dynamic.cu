@@ -9,7 +9,6 @@
 
 #include <algorithm>
 #include <cmath>
-#include <map>
 #include <string>
 #include <vector>
 
@@ -67,7 +66,8 @@ cudaError_t grow(void** p, size_t keep, size_t bytes, cudaStream_t s) {
 }
 
 // Device update after the host lists took the entries in `added` (row,
-// rank); c->n, c->rowp and c->succ already describe the grown cloud.
+// rank); c->n already counts the new sites. Rows are read from the
+// builder's lists.
 mknn_status update_device(mknn_cloud* c, int64_t n_old,
                           const std::vector<std::pair<int32_t, int32_t>>& added,
                           cudaStream_t s) {
@@ -90,24 +90,31 @@ mknn_status update_device(mknn_cloud* c, int64_t n_old,
   c->row_first.resize(n_new, 0);
   c->row_cap.resize(n_new, 0);
   // changed rows, each with its new tail or moved whole
-  std::map<int32_t, int32_t> grew;  // row -> entries added
-  for (const auto& a : added) grew[a.first]++;
-  std::vector<int32_t> pos, val, ridx;
+  std::vector<int32_t> rows_changed;
+  rows_changed.reserve(added.size());
+  for (const auto& a : added) rows_changed.push_back(a.first);
+  std::sort(rows_changed.begin(), rows_changed.end());
+  std::vector<int32_t> pos, val, ridx, tail;
   std::vector<int2> rval;
-  for (const auto& g : grew) {
-    const int32_t i = g.first;
-    const int64_t b = c->rowp[i], len = c->rowp[i + 1] - b, len_old = len - g.second;
+  for (size_t a = 0; a < rows_changed.size();) {
+    const int32_t i = rows_changed[a];
+    size_t b = a;
+    while (b < rows_changed.size() && rows_changed[b] == i) ++b;
+    const int64_t len = c->inc->row_len(i), len_old = len - (int64_t)(b - a);
+    a = b;
     int64_t from = len_old;
     if (len > c->row_cap[i]) {  // no room: the whole row moves to the arena top
-      const int64_t cap = std::max<int64_t>(2 * len, 16);
+      const int64_t cap = len + len / 2 + 4;
       c->row_first[i] = c->ent_top;
       c->row_cap[i] = cap;
       c->ent_top += cap;
       from = 0;
     }
-    for (int64_t t = from; t < len; ++t) {
-      pos.push_back((int32_t)(c->row_first[i] + t));
-      val.push_back(c->succ[b + t]);
+    tail.clear();
+    c->inc->row_tail(i, from, &tail);
+    for (size_t t = 0; t < tail.size(); ++t) {
+      pos.push_back((int32_t)(c->row_first[i] + from + (int64_t)t));
+      val.push_back(tail[t]);
     }
     ridx.push_back(i);
     rval.push_back(make_int2((int32_t)c->row_first[i], (int32_t)(c->row_first[i] + len)));
@@ -167,6 +174,49 @@ mknn_status update_device(mknn_cloud* c, int64_t n_old,
   return MKNN_OK;
 }
 
+// Lays the device table out afresh from the host CSR: rows contiguous in
+// rank order, each with room equal to its length, the arena's headroom
+// after them.
+mknn_status compact_device(mknn_cloud* c, cudaStream_t s) {
+  c->sync_csr();
+  const int64_t n = c->n, E = (int64_t)c->succ.size();
+  const int64_t cap = std::max<int64_t>(E + std::max<int64_t>(E / 4, 1 << 16), 1);
+  if (cap >= (int64_t)0x7FFFFFFF) return afail(MKNN_ENOMEM, "entry arena exceeds 2^31 entries");
+  std::vector<int2> rows((size_t)n);
+  for (int64_t i = 0; i < n; ++i) {
+    rows[i] = make_int2((int32_t)c->rowp[i], (int32_t)c->rowp[i + 1]);
+    c->row_first[i] = c->rowp[i];
+    c->row_cap[i] = c->rowp[i + 1] - c->rowp[i];
+  }
+  int32_t* succ = nullptr;
+  void* ent = nullptr;
+  cudaError_t e;
+  if ((e = cudaMalloc((void**)&succ, (size_t)cap * 4)) != cudaSuccess ||
+      (e = cudaMalloc(&ent, (size_t)cap * 16)) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(succ);
+    return afail(MKNN_ENOMEM, std::string("compacting the entry arena: ") + cudaGetErrorString(e));
+  }
+  e = cudaMemcpyAsync(succ, c->succ.data(), (size_t)E * 4, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = launch_fill_entries(c->d_pts, succ, E, ent, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->d_rows, rows.data(), (size_t)n * 8, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    cudaFree(succ);
+    cudaFree(ent);
+    return afail(MKNN_ECUDA, std::string("compacting the entry arena: ") + cudaGetErrorString(e));
+  }
+  cudaFree(c->d_succ);
+  cudaFree(c->d_ent);
+  c->d_succ = succ;
+  c->d_ent = ent;
+  c->dev_bytes = c->dev_bytes - (size_t)c->ent_cap * 20 + (size_t)cap * 20;
+  c->ent_cap = cap;
+  c->ent_top = E;
+  return MKNN_OK;
+}
+
 }  // namespace
 
 }  // namespace mknn
@@ -197,11 +247,11 @@ mknn_status mknn_cloud_append(mknn_cloud* c, const float* xyz, int64_t count,
     std::string err;
     if (!c->inc->append(c->xyz.data(), n_new, &added, &err)) return afail(MKNN_EINVAL, err);
     c->n = n_new;
-    c->inc->csr(&c->rowp, &c->succ);
+    c->csr_stale.store(true);
   } catch (const std::bad_alloc&) {
     return afail(MKNN_ENOMEM, "host allocation failed while appending");
   }
-  if ((int64_t)c->succ.size() >= (int64_t)0x7FFFFFFF)
+  if (c->inc->entries() >= (int64_t)0x7FFFFFFF)
     return afail(MKNN_EINVAL, "successor table exceeds 2^31 entries");
   const double secs = c->stats.seconds;
   c->stats = c->inc->stats();
@@ -217,7 +267,13 @@ mknn_status mknn_cloud_append(mknn_cloud* c, const float* xyz, int64_t count,
   int cur = 0;
   cudaGetDevice(&cur);
   if (cur != c->device) cudaSetDevice(c->device);
-  const mknn_status st = update_device(c, n_old, added, (cudaStream_t)stream);
+  mknn_status st = update_device(c, n_old, added, (cudaStream_t)stream);
+  // moved rows leave their old copies behind: once the arena holds twice
+  // the live entries, the table is laid out afresh (contiguous rows, as
+  // after an upload), which keeps the entries of a row and of neighbouring
+  // rows dense in cache lines
+  if (st == MKNN_OK && c->ent_top > 2 * c->inc->entries() + (1 << 16))
+    st = compact_device(c, (cudaStream_t)stream);
   if (cur != c->device) cudaSetDevice(cur);
   return st;
 }
