@@ -61,6 +61,7 @@ struct Lists {
   };
   std::vector<Block> pool;
   std::vector<int32_t> head, tail, len;
+  int64_t total = 0, longest = 0;
 
   void init(int64_t n) {
     head.assign(n, -1);
@@ -89,6 +90,8 @@ struct Lists {
     }
     pool[t].e[pool[t].cnt++] = j;
     len[i]++;
+    total++;
+    if (len[i] > longest) longest = len[i];
   }
 };
 
@@ -113,11 +116,7 @@ class Builder {
   void csr(std::vector<int64_t>* rowp, std::vector<int32_t>* succ) const;
   int32_t size() const { return n_; }
   int64_t row_len(int32_t i) const { return L_.len[i]; }
-  int64_t longest_row() const {
-    int64_t mx = 0;
-    for (int32_t i = 0; i < n_; ++i) mx = std::max<int64_t>(mx, L_.len[i]);
-    return mx;
-  }
+  int64_t longest_row() const { return L_.longest; }
   void row_tail(int32_t i, int64_t from, std::vector<int32_t>* out) const {
     int64_t at = 0;
     for (int32_t bk = L_.head[i]; bk >= 0; bk = L_.pool[bk].next)
@@ -479,9 +478,7 @@ bool Builder::append(const float* xyz, int32_t n_new,
   for (int32_t j = n_old; j < n_new && ok; ++j) ok = insert_rank(j, err);
   added_ = nullptr;
   st_.n = n_;
-  int64_t e = 0;
-  for (int32_t i = 0; i < n_; ++i) e += L_.len[i];
-  st_.entries = e;
+  st_.entries = L_.total;
   return ok;
 }
 

@@ -25,6 +25,26 @@ thread_local std::string g_err;
 }
 
 void set_error(const std::string& msg) { g_err = msg; }
+
+cudaError_t upload_entries(const mknn_cloud* c, int32_t* d_succ, void* d_ent, int64_t slack,
+                           cudaStream_t s) {
+  const int64_t n = c->n, E = (int64_t)c->succ.size();
+  const int64_t total = E + slack * n;
+  if (total <= 0) return cudaSuccess;
+  cudaError_t e;
+  if (slack == 0) {
+    e = cudaMemcpyAsync(d_succ, c->succ.data(), (size_t)E * 4, cudaMemcpyHostToDevice, s);
+  } else {
+    std::vector<int32_t> spaced((size_t)total, 0);  // empty slots hold rank 0 (never read)
+    for (int64_t i = 0; i < n; ++i)
+      std::copy(c->succ.begin() + c->rowp[i], c->succ.begin() + c->rowp[i + 1],
+                spaced.begin() + c->rowp[i] + slack * i);
+    e = cudaMemcpyAsync(d_succ, spaced.data(), (size_t)total * 4, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // before `spaced` goes
+  }
+  if (e != cudaSuccess) return e;
+  return launch_fill_entries(c->d_pts, d_succ, total, d_ent, s);
+}
 const char* get_error() { return g_err.c_str(); }
 
 namespace {
@@ -268,8 +288,10 @@ mknn_status mknn_cloud_upload(mknn_cloud* c, mknn_stream_t stream) {
   const int64_t n = c->n, E = c->E();
   // a dynamic cloud gets headroom for appended sites and entries
   const bool dyn = (bool)c->inc;
+  const int64_t slack = dyn ? kRowSlack : 0;  // room for appends in every row
   const int64_t pcap = dyn ? n + std::max<int64_t>(n / 4, 4096) : n;
-  const int64_t ecap = std::max<int64_t>(dyn ? E + std::max<int64_t>(E / 4, 1 << 16) : E, 1);
+  const int64_t ecap =
+      std::max<int64_t>(dyn ? E + slack * n + std::max<int64_t>(E / 4, 1 << 16) : E, 1);
   if (ecap >= (int64_t)0x7FFFFFFF) return fail(MKNN_EINVAL, "entry arena exceeds 2^31 entries");
   std::vector<float> p4;
   std::vector<int2> rows;
@@ -288,10 +310,11 @@ mknn_status mknn_cloud_upload(mknn_cloud* c, mknn_stream_t stream) {
     p4[4 * i + 1] = c->xyz[3 * i + 1];
     p4[4 * i + 2] = c->xyz[3 * i + 2];
     p4[4 * i + 3] = 0.f;
-    rows[i] = make_int2((int32_t)c->rowp[i], (int32_t)c->rowp[i + 1]);
+    const int64_t first = c->rowp[i] + slack * i, len = c->rowp[i + 1] - c->rowp[i];
+    rows[i] = make_int2((int32_t)first, (int32_t)(first + len));
     if (dyn) {
-      c->row_first[i] = c->rowp[i];
-      c->row_cap[i] = c->rowp[i + 1] - c->rowp[i];
+      c->row_first[i] = first;
+      c->row_cap[i] = len + slack;
     }
   }
   c->device = cur;
@@ -311,9 +334,7 @@ mknn_status mknn_cloud_upload(mknn_cloud* c, mknn_stream_t stream) {
           cudaSuccess ||
       (e = cudaMemcpyAsync(c->d_rows, rows.data(), (size_t)n * 8, cudaMemcpyHostToDevice, s)) !=
           cudaSuccess ||
-      (E > 0 && (e = cudaMemcpyAsync(c->d_succ, c->succ.data(), (size_t)E * 4,
-                                     cudaMemcpyHostToDevice, s)) != cudaSuccess) ||
-      (E > 0 && (e = launch_fill_entries(c->d_pts, c->d_succ, E, c->d_ent, s)) != cudaSuccess) ||
+      (E > 0 && (e = upload_entries(c, c->d_succ, c->d_ent, slack, s)) != cudaSuccess) ||
       (e = cudaMemsetAsync(c->d_err, 0, 256, s)) != cudaSuccess ||
       (e = cudaStreamSynchronize(s)) != cudaSuccess) {
     free_device(c);
@@ -321,7 +342,7 @@ mknn_status mknn_cloud_upload(mknn_cloud* c, mknn_stream_t stream) {
   }
   c->pts_cap = pcap;
   c->ent_cap = ecap;
-  c->ent_top = E;
+  c->ent_top = E + slack * n;
   c->dev_bytes = b_pts + b_rows + b_succ + b_ent + 256;
   return MKNN_OK;
 }

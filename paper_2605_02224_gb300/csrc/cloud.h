@@ -86,6 +86,13 @@ struct mknn_cloud {
 };
 
 namespace mknn {
+// Empty slots left after every row of a dynamic cloud when its table is laid
+// out (upload, compaction), so that most rows take a few appends in place.
+constexpr int64_t kRowSlack = 2;
+// Writes the cloud's CSR into device arrays, `slack` empty slots after each
+// row (row i starts at rowp[i] + slack * i), and fills ent from it.
+cudaError_t upload_entries(const mknn_cloud* c, int32_t* d_succ, void* d_ent, int64_t slack,
+                           cudaStream_t s);
 void set_error(const std::string& msg);
 const char* get_error();
 }  // namespace mknn

@@ -104,7 +104,7 @@ mknn_status update_device(mknn_cloud* c, int64_t n_old,
     a = b;
     int64_t from = len_old;
     if (len > c->row_cap[i]) {  // no room: the whole row moves to the arena top
-      const int64_t cap = len + len / 2 + 4;
+      const int64_t cap = len + len / 4 + kRowSlack;
       c->row_first[i] = c->ent_top;
       c->row_cap[i] = cap;
       c->ent_top += cap;
@@ -174,19 +174,19 @@ mknn_status update_device(mknn_cloud* c, int64_t n_old,
   return MKNN_OK;
 }
 
-// Lays the device table out afresh from the host CSR: rows contiguous in
-// rank order, each with room equal to its length, the arena's headroom
-// after them.
+// Lays the device table out afresh from the host CSR: rows in rank order,
+// each followed by kRowSlack empty slots, the arena's headroom after them.
 mknn_status compact_device(mknn_cloud* c, cudaStream_t s) {
   c->sync_csr();
-  const int64_t n = c->n, E = (int64_t)c->succ.size();
-  const int64_t cap = std::max<int64_t>(E + std::max<int64_t>(E / 4, 1 << 16), 1);
+  const int64_t n = c->n, E = (int64_t)c->succ.size(), fresh = E + kRowSlack * n;
+  const int64_t cap = std::max<int64_t>(fresh + std::max<int64_t>(E / 4, 1 << 16), 1);
   if (cap >= (int64_t)0x7FFFFFFF) return afail(MKNN_ENOMEM, "entry arena exceeds 2^31 entries");
   std::vector<int2> rows((size_t)n);
   for (int64_t i = 0; i < n; ++i) {
-    rows[i] = make_int2((int32_t)c->rowp[i], (int32_t)c->rowp[i + 1]);
-    c->row_first[i] = c->rowp[i];
-    c->row_cap[i] = c->rowp[i + 1] - c->rowp[i];
+    const int64_t first = c->rowp[i] + kRowSlack * i, len = c->rowp[i + 1] - c->rowp[i];
+    rows[i] = make_int2((int32_t)first, (int32_t)(first + len));
+    c->row_first[i] = first;
+    c->row_cap[i] = len + kRowSlack;
   }
   int32_t* succ = nullptr;
   void* ent = nullptr;
@@ -197,8 +197,7 @@ mknn_status compact_device(mknn_cloud* c, cudaStream_t s) {
     cudaFree(succ);
     return afail(MKNN_ENOMEM, std::string("compacting the entry arena: ") + cudaGetErrorString(e));
   }
-  e = cudaMemcpyAsync(succ, c->succ.data(), (size_t)E * 4, cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = launch_fill_entries(c->d_pts, succ, E, ent, s);
+  e = upload_entries(c, succ, ent, kRowSlack, s);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(c->d_rows, rows.data(), (size_t)n * 8, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -213,7 +212,7 @@ mknn_status compact_device(mknn_cloud* c, cudaStream_t s) {
   c->d_ent = ent;
   c->dev_bytes = c->dev_bytes - (size_t)c->ent_cap * 20 + (size_t)cap * 20;
   c->ent_cap = cap;
-  c->ent_top = E;
+  c->ent_top = fresh;
   return MKNN_OK;
 }
 
@@ -268,11 +267,12 @@ mknn_status mknn_cloud_append(mknn_cloud* c, const float* xyz, int64_t count,
   cudaGetDevice(&cur);
   if (cur != c->device) cudaSetDevice(c->device);
   mknn_status st = update_device(c, n_old, added, (cudaStream_t)stream);
-  // moved rows leave their old copies behind: once the arena holds twice
-  // the live entries, the table is laid out afresh (contiguous rows, as
-  // after an upload), which keeps the entries of a row and of neighbouring
-  // rows dense in cache lines
-  if (st == MKNN_OK && c->ent_top > 2 * c->inc->entries() + (1 << 16))
+  // moved rows leave their old copies behind: once the arena is 40% larger
+  // than a fresh layout would be, the table is laid out afresh (rows in
+  // rank order, as after an upload), which keeps the live entries dense in
+  // cache lines (queries read through L2)
+  const int64_t fresh = c->inc->entries() + kRowSlack * c->n;
+  if (st == MKNN_OK && c->ent_top > fresh + fresh * 2 / 5 + (1 << 16))
     st = compact_device(c, (cudaStream_t)stream);
   if (cur != c->device) cudaSetDevice(cur);
   return st;
