@@ -543,6 +543,11 @@ def dynamic_workload(args, M, torch):
     t_dyn, i1, d1 = timed(c)
     t_sta, i2, d2 = timed(static)
     same = bool(torch.equal(i1, i2) and torch.equal(d1, d2))
+    t1 = time.perf_counter()
+    c.compact(s)
+    compact_ms = (time.perf_counter() - t1) * 1e3
+    t_cmp, i3, d3 = timed(c)
+    same = same and bool(torch.equal(i1, i3) and torch.equal(d1, d3))
     line = {"metric": "appended points/sec (dynamic 1M-pt torus, host insertion + device update)",
             "value": appended / (sum(ms) / 1e3), "unit": "points/s", "n_gpus": 1,
             "higher_is_better": True, "data": "synthetic", "dtype": "f32",
@@ -553,6 +558,8 @@ def dynamic_workload(args, M, torch):
                                    "max": float(np.max(ms)), "calls": len(ms)},
             "queries_after_appends": {"value": nq / (t_dyn / 1e3), "ms_per_step": t_dyn},
             "queries_static_build": {"value": nq / (t_sta / 1e3), "ms_per_step": t_sta},
+            "queries_after_compact": {"value": nq / (t_cmp / 1e3), "ms_per_step": t_cmp,
+                                      "compact_ms": compact_ms},
             "results_identical": same,
             "device_bytes": {"dynamic": c.device_bytes(), "static": static.device_bytes()}}
     print(json.dumps(line), flush=True)

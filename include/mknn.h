@@ -126,6 +126,17 @@ mknn_status mknn_cloud_upload(mknn_cloud* cloud, mknn_stream_t stream);
 mknn_status mknn_cloud_append(mknn_cloud* cloud, const float* xyz, int64_t count,
                               mknn_stream_t stream);
 
+/* mknn_cloud_compact: lays a dynamic cloud's device table out afresh (rows
+ * in rank order, each followed by two empty slots), dropping the copies
+ * that appends left behind. Appends do this on their own once the table has
+ * grown 40% beyond a fresh layout; calling it after a burst of appends
+ * brings queries back to the speed of a fresh upload. Synchronises the
+ * stream; the same rules as for mknn_cloud_append apply (no overlapping
+ * queries on other streams; the entry arrays move, so batch plans made
+ * before it must be recreated). Errors: EINVAL (not dynamic or not
+ * uploaded), ENOMEM, ECUDA. */
+mknn_status mknn_cloud_compact(mknn_cloud* cloud, mknn_stream_t stream);
+
 /* Releases device memory of the cloud (keeps the host copy). */
 mknn_status mknn_cloud_release_device(mknn_cloud* cloud);
 

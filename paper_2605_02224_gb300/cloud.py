@@ -33,6 +33,11 @@ class Cloud:
         M.mknn_cloud_append(self.handle, xyz, stream)
         return self
 
+    def compact(self, stream: int = 0) -> "Cloud":
+        """Lays a dynamic cloud's device table out afresh."""
+        M.mknn_cloud_compact(self.handle, stream)
+        return self
+
     def upload(self, stream: int = 0) -> "Cloud":
         M.mknn_cloud_upload(self.handle, stream)
         return self

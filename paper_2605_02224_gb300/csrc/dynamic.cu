@@ -278,4 +278,18 @@ mknn_status mknn_cloud_append(mknn_cloud* c, const float* xyz, int64_t count,
   return st;
 }
 
+mknn_status mknn_cloud_compact(mknn_cloud* c, mknn_stream_t stream) {
+  if (!c) return afail(MKNN_EINVAL, "cloud is NULL");
+  if (!c->inc) return afail(MKNN_EINVAL, "the cloud was not built with the dynamic option");
+  std::lock_guard<std::mutex> lk(c->mu);
+  if (!c->d_pts) return afail(MKNN_EINVAL, "cloud is not uploaded");
+  int cur = 0;
+  cudaGetDevice(&cur);
+  if (cur != c->device) cudaSetDevice(c->device);
+  const mknn_status st = compact_device(c, (cudaStream_t)stream);
+  c->generation.fetch_add(1);  // the entry arrays moved
+  if (cur != c->device) cudaSetDevice(cur);
+  return st;
+}
+
 }  // extern "C"

@@ -120,6 +120,7 @@ def _declare(L):
         "mknn_knn_host": (i32, [vp, vp, i64, i32, i32, vp, i32, vp, vp, vp]),
         "mknn_knn_sites": (i32, [vp, vp, i64, i32, vp, i32, vp, vp, vp, vp]),
         "mknn_cloud_append": (i32, [vp, vp, i64, vp]),
+        "mknn_cloud_compact": (i32, [vp, vp]),
         "mknn_knn_sites_workspace_size": (C.c_size_t, [i64, vp]),
         "mknn_cloud_check": (i32, [vp, vp]),
         "mknn_query_order_workspace_size": (sz, [i64]),
@@ -193,6 +194,10 @@ def mknn_cloud_append(cloud: int, xyz, stream: int = 0):
     built with dynamic=True."""
     x = _host(xyz, np.float32).reshape(-1, 3)
     _check(lib().mknn_cloud_append(cloud, _ptr(x), x.shape[0], stream or None))
+
+
+def mknn_cloud_compact(cloud: int, stream: int = 0):
+    _check(lib().mknn_cloud_compact(cloud, stream or None))
 
 
 def mknn_cloud_from_table(xyz_ranked, rowp, succ) -> int:

@@ -346,6 +346,8 @@ def test_append_errors_leave_the_cloud_unchanged():
     with pytest.raises(M.MknnError) as ei:
         static.append(P[:3])
     assert ei.value.status == 1                        # EINVAL: not dynamic
+    with pytest.raises(M.MknnError):
+        static.compact()
     c = Cloud.build(P, dynamic=True)
     bad = np.array([[0.1, 0.2, np.nan]], np.float32)
     with pytest.raises(M.MknnError):

@@ -51,6 +51,11 @@ def test_appends_equal_one_build_on_the_device(torch):
         assert np.array_equal(old[0], before[0]) and np.array_equal(old[1], before[1])
         ref.close()
     assert c.device_bytes() > bytes0
+    a = run_knn(c, Q, 16)
+    c.compact()
+    b = run_knn(c, Q, 16)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    c.append(Pr[:0])
     idx, d2 = run_knn(c, Q, 16)
     parity.check_rows(Pr, Q, 16, 0, idx, d2, rows=range(0, 3000, 10))
     m = np.clip(np.floor(np.exp(W.uniform(8, 1, 3000) * np.log(20000))), 1, 20000)
