@@ -54,7 +54,7 @@ def _args():
     ap.add_argument("--no-serve", action="store_true", help="skip the serving section")
     ap.add_argument("--serve-requests", type=int, default=400)
     ap.add_argument("--workload", default="torus",
-                    choices=["torus", "batch", "prefix", "sites", "dynamic"])
+                    choices=["torus", "batch", "prefix", "sites", "dynamic", "sweep"])
     ap.add_argument("--append-batch", type=int, default=10000,
                     help="dynamic workload: points per append call")
     return ap.parse_args()
@@ -565,6 +565,60 @@ def dynamic_workload(args, M, torch):
     print(json.dumps(line), flush=True)
 
 
+def sweep_workload(args, M, torch):
+    """Sensitivity to manifold structure: the 1M-point bumpy sphere with
+    every point displaced by up to a fraction of its bbox diagonal, and
+    points uniform in a cube (queries in the same cube), 4M queries, k = 16:
+    queries/s, successor-list shape and work per query for each."""
+    import workloads as W
+    wls = [W.degraded_bumpy(r, args.n, args.nq, args.k)
+           for r in (0.0, 0.001, 0.003, 0.01, 0.03, 0.1)]
+    wls += [W.uniform_volume(n, args.nq, args.k) for n in (100_000, args.n)]
+    clouds, build_s = _build_many(wls, "sweep")
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream(dev)
+    s = stream.cuda_stream
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    runs = []
+    for wl, c in zip(wls, clouds):
+        c.upload(s)
+        q = torch.from_numpy(wl.queries).to(dev)
+        nq, k = wl.nq, wl.k
+        idx = torch.empty((nq, k), dtype=torch.int32, device=dev)
+        d2 = torch.empty((nq, k), dtype=torch.float32, device=dev)
+        for _ in range(max(3, args.warmup)):
+            M.mknn_knn(c.handle, q, nq, 3, k, None, 0, idx, d2, s)
+        cnt = torch.zeros((nq, 4), dtype=torch.int32, device=dev)
+        M.mknn_knn_ex(c.handle, q, nq, 3, k, None, 0, idx, d2, s, counters=cnt, lanes=1,
+                      placement=1)
+        torch.cuda.synchronize()
+        rows, entries, coords, trans = (int(x) for x in cnt.to(torch.int64).sum(dim=0).cpu())
+        ms = []
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            M.mknn_knn(c.handle, q, nq, 3, k, None, 0, idx, d2, s)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        _, rowp, _ = c.table()
+        L = np.diff(rowp)
+        runs.append({"workload": wl.name, "displacement_ratio": wl.meta.get("ratio"),
+                     "value": nq / (float(np.mean(ms)) / 1e3), "ms_per_step": float(np.mean(ms)),
+                     "E_per_site": float(L.mean()), "longest_row": int(L.max()),
+                     "per_query": {"rows": rows / nq, "entries": entries / nq,
+                                   "transitions": trans / nq}})
+        c.close()
+    line = {"metric": "k-NN queries/sec vs manifold degradation (1M-pt bumpy sphere, k=16)",
+            "value": runs[0]["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": True, "data": "synthetic", "dtype": "f32",
+            "config": {"l2": "flushed before every timed step",
+                       "build_seconds_max": build_s if build_s is not None else "cached"},
+            "runs": runs}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = _args()
     rank, world, local = _dist_env()
@@ -587,6 +641,9 @@ def main():
         return
     if args.workload == "dynamic":
         dynamic_workload(args, M, torch)
+        return
+    if args.workload == "sweep":
+        sweep_workload(args, M, torch)
         return
     dist = None
     if world > 1:

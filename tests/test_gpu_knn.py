@@ -191,6 +191,26 @@ def test_large_k_with_prefix_bounds():
     c.close()
 
 
+@pytest.mark.parametrize("ratio", [0.003, 0.03, 0.1, "uniform"])
+def test_degraded_manifold_and_uniform_volume(ratio):
+    """The sensitivity study's inputs at 20,000 sites: a bumpy sphere with
+    every point displaced by up to a fraction of its bbox diagonal, and
+    points uniform in a cube with queries in the same cube. Every row
+    against the oracle for the default kernel; other variants identical."""
+    if ratio == "uniform":
+        wl = W.uniform_volume(20000, 2000, 16)
+    else:
+        wl = W.degraded_bumpy(ratio, 20000, 2000, 16)
+    c = Cloud.build(wl.points, wl.order).upload()
+    Pr = wl.ranked_points()
+    idx, d2 = run_knn(c, wl.queries, 16)
+    parity.check_rows(Pr, wl.queries, 16, 0, idx, d2)
+    for v in (dict(lanes=1, placement=1), dict(lanes=32, placement=1)):
+        i2, d22 = run_knn(c, wl.queries, 16, **v)
+        assert np.array_equal(i2, idx) and np.array_equal(d22, d2)
+    c.close()
+
+
 def test_invalid_per_query_m_sets_flag_and_pads():
     import torch
     wl = W.small_sphere(nq=64)

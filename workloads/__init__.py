@@ -10,9 +10,9 @@ transcendental functions.
 from .gen import (  # noqa: F401
     rand_u64, uniform, normal, permutation,
     sphere, torus, bumpy_sphere, patches4, lattice, uniform_cube,
-    box_queries, near_surface_queries, bbox, SURFACES, surface,
+    box_queries, near_surface_queries, bbox, SURFACES, surface, displace,
 )
 from .configs import (  # noqa: F401
     Workload, small_sphere, large_torus, prefix_bumpy, batch_clouds,
-    serve_clouds, serve_requests, padded_box, Request,
+    serve_clouds, serve_requests, padded_box, Request, degraded_bumpy, uniform_volume,
 )

@@ -63,6 +63,28 @@ def large_torus(n: int = 1_000_000, nq: int = 4_000_000, k: int = 16) -> Workloa
     return Workload(f"torus-{n}-q{nq}-k{k}", p, order, q, k=k, surface="torus")
 
 
+def degraded_bumpy(ratio: float, n: int = 1_000_000, nq: int = 4_000_000,
+                   k: int = 16) -> Workload:
+    """Bumpy sphere with every point displaced by up to `ratio` of the bbox
+    diagonal (ratio 0: the surface itself); queries in the padded bbox."""
+    p, _ = gen.bumpy_sphere(n, seed=51)
+    if ratio > 0:
+        p = gen.displace(p, ratio, seed=52)
+    order = gen.permutation(n, seed=53)
+    lo, hi = padded_box(p)
+    q = gen.box_queries(nq, 54, lo, hi)
+    return Workload(f"bumpy-displaced{ratio:g}-{n}", p, order, q, k=k, surface="bumpy",
+                    meta={"ratio": ratio})
+
+
+def uniform_volume(n: int = 1_000_000, nq: int = 4_000_000, k: int = 16) -> Workload:
+    """Targets and queries uniform in the same cube [-1, 1]^3 (no manifold)."""
+    p, _ = gen.uniform_cube(n, seed=61)
+    order = gen.permutation(n, seed=62)
+    q = gen.box_queries(nq, 63, [-1.0] * 3, [1.0] * 3)
+    return Workload(f"uniform-{n}", p, order, q, k=k, surface="uniform")
+
+
 def _mixed_queries(kind: str, p: np.ndarray, nq: int, seed: int) -> np.ndarray:
     """Half uniform in the padded box, half |N(0, 0.01)| off the surface."""
     lo, hi = padded_box(p)

@@ -149,6 +149,19 @@ def uniform_cube(n: int, seed: int, lo: float = -1.0, hi: float = 1.0, stream0: 
     return p.astype(np.float32), np.zeros((n, 3))
 
 
+def displace(p: np.ndarray, ratio: float, seed: int, stream0: int = 600) -> np.ndarray:
+    """Each point moved by a random vector: uniform direction, length
+    uniform in [0, ratio * d) with d the diagonal of the points' bounding
+    box (degrading the manifold structure, the sensitivity study of Sec. 5)."""
+    n = p.shape[0]
+    lo, hi = p.min(axis=0).astype(np.float64), p.max(axis=0).astype(np.float64)
+    d = float(np.linalg.norm(hi - lo))
+    v = _unit(np.stack([normal(seed, stream0, n), normal(seed, stream0 + 1, n),
+                        normal(seed, stream0 + 2, n)], axis=1))
+    length = ratio * d * uniform(seed, stream0 + 3, n)
+    return (p.astype(np.float64) + v * length[:, None]).astype(np.float32)
+
+
 SURFACES = ("sphere", "torus", "bumpy", "patches")
 
 
