@@ -54,7 +54,7 @@ def _args():
     ap.add_argument("--no-serve", action="store_true", help="skip the serving section")
     ap.add_argument("--serve-requests", type=int, default=400)
     ap.add_argument("--workload", default="torus",
-                    choices=["torus", "batch", "prefix", "sites", "dynamic", "sweep"])
+                    choices=["torus", "batch", "prefix", "sites", "dynamic", "sweep", "orders"])
     ap.add_argument("--append-batch", type=int, default=10000,
                     help="dynamic workload: points per append call")
     return ap.parse_args()
@@ -619,6 +619,76 @@ def sweep_workload(args, M, torch):
     print(json.dumps(line), flush=True)
 
 
+def orders_workload(args, M, torch):
+    """Insertion orders (Sec. 5): the 1M-point bumpy sphere built in a
+    random order, a BRIO round order with Hilbert-sorted rounds, and the
+    farthest-point order; the same 4M volume queries, k = 16, against each:
+    build time, list shape, work and speed per query."""
+    import workloads as W
+    from concurrent.futures import ThreadPoolExecutor
+    from paper_2605_02224_gb300 import Cloud
+    wl = W.degraded_bumpy(0.0, args.n, args.nq, args.k)
+    kinds = (("random", M.ORDER_RANDOM), ("brio_hilbert", M.ORDER_BRIO_HILBERT),
+             ("farthest_point", M.ORDER_FARTHEST_POINT))
+
+    def make(kind):
+        t0 = time.perf_counter()
+        o = M.mknn_insertion_order(wl.points, kind, 71)
+        t1 = time.perf_counter()
+        c = Cloud.build(wl.points, o)
+        return c, t1 - t0, time.perf_counter() - t1
+
+    with ThreadPoolExecutor(max_workers=3) as ex:
+        built = list(ex.map(lambda kk: make(kk[1]), kinds))
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream(dev)
+    s = stream.cuda_stream
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    q = torch.from_numpy(wl.queries).to(dev)
+    nq, k = wl.nq, wl.k
+    runs = []
+    ref = None
+    for (name, _), (c, order_s, build_s) in zip(kinds, built):
+        c.upload(s)
+        idx = torch.empty((nq, k), dtype=torch.int32, device=dev)
+        d2 = torch.empty((nq, k), dtype=torch.float32, device=dev)
+        for _ in range(max(3, args.warmup)):
+            M.mknn_knn(c.handle, q, nq, 3, k, None, 0, idx, d2, s)
+        cnt = torch.zeros((nq, 4), dtype=torch.int32, device=dev)
+        M.mknn_knn_ex(c.handle, q, nq, 3, k, None, 0, idx, d2, s, counters=cnt, lanes=1,
+                      placement=1)
+        torch.cuda.synchronize()
+        rows, entries, coords, trans = (int(x) for x in cnt.to(torch.int64).sum(dim=0).cpu())
+        ms = []
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            M.mknn_knn(c.handle, q, nq, 3, k, None, 0, idx, d2, s)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        # the same neighbours whatever the order (ranks differ: compare input indices)
+        inp = torch.from_numpy(c.order()).to(dev)[idx.long()]
+        same = True if ref is None else bool(torch.equal(inp, ref[0]) and torch.equal(d2, ref[1]))
+        if ref is None:
+            ref = (inp, d2.clone())
+        _, rowp, _ = c.table()
+        L = np.diff(rowp)
+        runs.append({"order": name, "order_seconds": order_s, "build_seconds": build_s,
+                     "value": nq / (float(np.mean(ms)) / 1e3), "ms_per_step": float(np.mean(ms)),
+                     "E_per_site": float(L.mean()), "longest_row": int(L.max()),
+                     "per_query": {"rows": rows / nq, "entries": entries / nq,
+                                   "transitions": trans / nq},
+                     "same_neighbours_as_random": same})
+        c.close()
+    line = {"metric": "k-NN queries/sec by insertion order (1M-pt bumpy sphere, k=16)",
+            "value": runs[0]["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": True, "data": "synthetic", "dtype": "f32",
+            "config": {"l2": "flushed before every timed step"}, "runs": runs}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = _args()
     rank, world, local = _dist_env()
@@ -644,6 +714,9 @@ def main():
         return
     if args.workload == "sweep":
         sweep_workload(args, M, torch)
+        return
+    if args.workload == "orders":
+        orders_workload(args, M, torch)
         return
     dist = None
     if world > 1:

@@ -82,6 +82,26 @@ typedef struct {
 mknn_status mknn_build(const float* xyz, int64_t n, const int64_t* order,
                        const mknn_build_opts* opts, mknn_cloud** out);
 
+/* mknn_insertion_order: a birth order for mknn_build (Sec. 5 compares
+ * insertion orders; the order changes the successor lists, hence build
+ * time and query work, never the answers). order_out receives n input
+ * indices, order_out[r] = the point to insert at rank r.
+ *   MKNN_ORDER_RANDOM         seeded uniform permutation.
+ *   MKNN_ORDER_BRIO_HILBERT   the seeded permutation cut into rounds of
+ *                             doubling size (the last holds half the points,
+ *                             the first at most 64), each round sorted along
+ *                             a 3D Hilbert curve over the bounding box.
+ *   MKNN_ORDER_FARTHEST_POINT each next point is the one farthest from those
+ *                             already taken (ties to the lower input index),
+ *                             from input index 0; seed unused.
+ * Host only. Errors: EINVAL (NULL, n < 0, non-finite coordinate, unknown
+ * kind), ENOMEM. */
+#define MKNN_ORDER_RANDOM 0
+#define MKNN_ORDER_BRIO_HILBERT 1
+#define MKNN_ORDER_FARTHEST_POINT 2
+mknn_status mknn_insertion_order(const float* xyz, int64_t n, int32_t kind, uint64_t seed,
+                                 int64_t* order_out);
+
 /* mknn_cloud_from_table: a cloud from an explicit successor table instead
  * of the builder. Any table whose rows are supersets of the true successor
  * lists gives exact results (extra entries are extra candidates), e.g. the
@@ -450,6 +470,11 @@ int32_t mknn_insphere_exact(const float* a, const float* b, const float* c, cons
  * oriented, *bad_sphere = (tetrahedron, site) pairs with the site strictly
  * inside the circumsphere. Both 0 for a valid Delaunay triangulation. */
 mknn_status mknn_cloud_validate(const mknn_cloud* cloud, int64_t* bad_orient, int64_t* bad_sphere);
+
+/* Position of the cell (x, y, z) of a 2^bits-per-axis grid along the 3D
+ * Hilbert curve that MKNN_ORDER_BRIO_HILBERT sorts by (1 <= bits <= 21;
+ * 0 otherwise). */
+uint64_t mknn_hilbert_index3(uint32_t x, uint32_t y, uint32_t z, int32_t bits);
 
 /* Library version string. */
 const char* mknn_version(void);

@@ -120,6 +120,8 @@ def _declare(L):
         "mknn_knn_host": (i32, [vp, vp, i64, i32, i32, vp, i32, vp, vp, vp]),
         "mknn_knn_sites": (i32, [vp, vp, i64, i32, vp, i32, vp, vp, vp, vp]),
         "mknn_cloud_append": (i32, [vp, vp, i64, vp]),
+        "mknn_insertion_order": (i32, [vp, i64, i32, C.c_uint64, vp]),
+        "mknn_hilbert_index3": (C.c_uint64, [C.c_uint32, C.c_uint32, C.c_uint32, i32]),
         "mknn_cloud_compact": (i32, [vp, vp]),
         "mknn_knn_sites_workspace_size": (C.c_size_t, [i64, vp]),
         "mknn_cloud_check": (i32, [vp, vp]),
@@ -198,6 +200,21 @@ def mknn_cloud_append(cloud: int, xyz, stream: int = 0):
 
 def mknn_cloud_compact(cloud: int, stream: int = 0):
     _check(lib().mknn_cloud_compact(cloud, stream or None))
+
+
+ORDER_RANDOM, ORDER_BRIO_HILBERT, ORDER_FARTHEST_POINT = 0, 1, 2
+
+
+def mknn_insertion_order(xyz, kind: int, seed: int = 0) -> np.ndarray:
+    """Birth order (int64 input indices by rank) of host points (n, 3)."""
+    x = _host(xyz, np.float32).reshape(-1, 3)
+    out = np.empty(x.shape[0], np.int64)
+    _check(lib().mknn_insertion_order(_ptr(x), x.shape[0], kind, seed, _ptr(out)))
+    return out
+
+
+def mknn_hilbert_index3(x: int, y: int, z: int, bits: int) -> int:
+    return int(lib().mknn_hilbert_index3(x, y, z, bits))
 
 
 def mknn_cloud_from_table(xyz_ranked, rowp, succ) -> int:
