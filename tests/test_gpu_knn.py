@@ -211,6 +211,23 @@ def test_degraded_manifold_and_uniform_volume(ratio):
     c.close()
 
 
+@pytest.mark.parametrize("kind", [M.ORDER_BRIO_HILBERT, M.ORDER_FARTHEST_POINT])
+def test_other_insertion_orders(kind):
+    """Clouds built in a BRIO/Hilbert or farthest-point order: every row
+    against the oracle, per-query m included (the prefix follows the order)."""
+    P, _ = W.bumpy_sphere(20000, 31)
+    order = M.mknn_insertion_order(P, kind, 9)
+    c = Cloud.build(P, order).upload()
+    Pr = P[order]
+    Q = np.concatenate([W.box_queries(1000, 33, [-1.3] * 3, [1.3] * 3),
+                        W.near_surface_queries("bumpy", 1000, 34)])
+    m = np.clip(np.floor(np.exp(W.uniform(35, 1, 2000) * np.log(20000))), 1, 20000).astype(np.int32)
+    for k, mm in ((16, None), (8, m)):
+        idx, d2 = run_knn(c, Q, k, mm)
+        parity.check_rows(Pr, Q, k, mm if mm is not None else 0, idx, d2)
+    c.close()
+
+
 def test_invalid_per_query_m_sets_flag_and_pads():
     import torch
     wl = W.small_sphere(nq=64)
