@@ -668,11 +668,12 @@ def orders_workload(args, M, torch):
             b.record(stream)
             torch.cuda.synchronize()
             ms.append(a.elapsed_time(b))
-        # the same neighbours whatever the order (ranks differ: compare input indices)
-        inp = torch.from_numpy(c.order()).to(dev)[idx.long()]
-        same = True if ref is None else bool(torch.equal(inp, ref[0]) and torch.equal(d2, ref[1]))
+        # the same distances whatever the order (equal float32 distances are
+        # ordered by rank, which the order changes, so neighbours are
+        # compared through their distances)
+        same = True if ref is None else bool(torch.equal(d2, ref))
         if ref is None:
-            ref = (inp, d2.clone())
+            ref = d2.clone()
         _, rowp, _ = c.table()
         L = np.diff(rowp)
         runs.append({"order": name, "order_seconds": order_s, "build_seconds": build_s,
@@ -680,7 +681,7 @@ def orders_workload(args, M, torch):
                      "E_per_site": float(L.mean()), "longest_row": int(L.max()),
                      "per_query": {"rows": rows / nq, "entries": entries / nq,
                                    "transitions": trans / nq},
-                     "same_neighbours_as_random": same})
+                     "same_distances_as_random": same})
         c.close()
     line = {"metric": "k-NN queries/sec by insertion order (1M-pt bumpy sphere, k=16)",
             "value": runs[0]["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
