@@ -45,6 +45,8 @@ def _args():
     ap.add_argument("--lanes", type=int, default=0)
     ap.add_argument("--nq", type=int, default=4_000_000)
     ap.add_argument("--k", type=int, default=16)
+    ap.add_argument("--blocks-per-sm", type=int, default=0,
+                    help="resident query blocks per SM (0 = as many as fit)")
     ap.add_argument("--placement", type=int, default=0,
                     help="one-lane candidate lists: 0 default, 1 registers, 2 shared memory")
     ap.add_argument("--n", type=int, default=1_000_000)
@@ -752,7 +754,7 @@ def main():
         if ev:
             ev[1].record(stream)
         M.mknn_knn_ex(cloud.handle, q, nq, 3, k, None, 0, idx, d2, sptr, lanes=lanes, order=order,
-                      sort=sort_flag, placement=args.placement)
+                      sort=sort_flag, placement=args.placement, blocks_per_sm=args.blocks_per_sm)
         if ev:
             ev[2].record(stream)
 
