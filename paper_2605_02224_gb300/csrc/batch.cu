@@ -90,7 +90,7 @@ __device__ __forceinline__ void serve_item_smem(const ReqDev& R, const Item& w, 
       atomicOr(R.err, 1);
       continue;
     }
-    knn_query_smem<W>(C, qx, qy, qz, R.k, m, col, oi, od);
+    knn_query_smem<W>(C, qx, qy, qz, R.k, m, col, R.out_idx, R.out_d2, (int32_t)qi);
   }
 }
 
@@ -230,11 +230,11 @@ void set_smem_attributes() {
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)list_bytes(256, 32));
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(knn_batch_smem_kernel<128, 1>,
+    e = cudaFuncSetAttribute(knn_batch_smem_kernel<128, 2>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)list_bytes(128, 64));
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(knn_batch_smem_kernel<64, 2>,
+    e = cudaFuncSetAttribute(knn_batch_smem_kernel<64, 4>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)list_bytes(64, 128));
   g_attr_err = e;
@@ -259,8 +259,8 @@ const void* variant_kernel(int variant, int threads) {
     case 14: return (const void*)knn_batch_group_kernel<32, 4>;
     case kSmemVariant:
       return threads == 256 ? (const void*)knn_batch_smem_kernel<256, 1>
-                            : (const void*)knn_batch_smem_kernel<128, 1>;
-    case kSmemVariant128: return (const void*)knn_batch_smem_kernel<64, 2>;
+                            : (const void*)knn_batch_smem_kernel<128, 2>;
+    case kSmemVariant128: return (const void*)knn_batch_smem_kernel<64, 4>;
     default: return nullptr;
   }
 }

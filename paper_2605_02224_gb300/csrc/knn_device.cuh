@@ -519,12 +519,23 @@ __device__ __forceinline__ uint64_t pack_key(float d, uint32_t r) {
   return ((uint64_t)__float_as_uint(d) << 32) | r;
 }
 
-// W 64-bit words of expanded flags: W = 1 for k <= 64, 2 for k <= 128.
+// Expanded flags, one bit per list position, in W 32-bit words: W = 1 for
+// k <= 32 (one 32-bit register), 2 for k <= 64 (one 64-bit), 4 for k <= 128
+// (two 64-bit).
+template <int W>
+struct Flags {
+  uint64_t lo = 0, hi = 0;
+};
+template <>
+struct Flags<1> {
+  uint32_t lo = 0;
+};
+
 template <int W>
 struct SmemList {
   uint64_t* col;   // this lane's column: col[i * 32]
   int cnt;
-  uint64_t done[W];  // bit i of the flags: entry at position i expanded
+  Flags<W> done;   // bit i: entry at position i expanded
   uint64_t worst;  // key of position k-1 (a pad while cnt < k)
 };
 
@@ -532,53 +543,64 @@ template <int W>
 __device__ __forceinline__ void slist_init(SmemList<W>& L, uint64_t* col) {
   L.col = col;
   L.cnt = 0;
-#pragma unroll
-  for (int w = 0; w < W; ++w) L.done[w] = 0ull;
+  L.done = Flags<W>{};
   L.worst = pack_key(__int_as_float(0x7f800000), kRankMask);
 }
 
-// Opens a clear flag at position pos: flags at pos and above move up one.
-__device__ __forceinline__ uint64_t flags_open(uint64_t f, int pos) {
-  const uint64_t low = pos ? (f & (~0ull >> (64 - pos))) : 0ull;
+// Opens a clear flag at bit pos of one word: bits at pos and above move up.
+template <typename T>
+__device__ __forceinline__ T flags_open(T f, int pos) {
+  const T low = pos ? (f & (~T(0) >> (8 * sizeof(T) - pos))) : T(0);
   return low | ((f >> pos) << 1 << pos);
 }
 
+// Opens a clear flag at list position pos (an insertion there).
 template <int W>
 __device__ __forceinline__ void flags_insert(SmemList<W>& L, int pos) {
-  if constexpr (W == 1) {
-    L.done[0] = flags_open(L.done[0], pos);
-  } else {
+  if constexpr (W == 4) {
     if (pos < 64) {
-      const uint64_t carry = L.done[0] >> 63;
-      L.done[0] = flags_open(L.done[0], pos);
-      L.done[1] = (L.done[1] << 1) | carry;
+      L.done.hi = (L.done.hi << 1) | (L.done.lo >> 63);
+      L.done.lo = flags_open(L.done.lo, pos);
     } else {
-      L.done[1] = flags_open(L.done[1], pos - 64);
+      L.done.hi = flags_open(L.done.hi, pos - 64);
     }
+  } else {
+    L.done.lo = flags_open(L.done.lo, pos);
   }
 }
 
 // Position of the first entry among the first lim not yet expanded, or -1.
 template <int W>
 __device__ __forceinline__ int flags_first_clear(const SmemList<W>& L, int lim) {
-  const int l0 = min(lim, 64);
-  const uint64_t c0 = ~L.done[0] & (l0 == 64 ? ~0ull : ((1ull << l0) - 1ull));
-  if (c0) return __ffsll((long long)c0) - 1;
-  if constexpr (W == 2) {
-    if (lim > 64) {
-      const uint64_t c1 = ~L.done[1] & ((1ull << (lim - 64)) - 1ull);
-      if (c1) return 64 + __ffsll((long long)c1) - 1;
+  if constexpr (W == 1) {
+    const uint32_t c = ~L.done.lo & ((1u << lim) - 1u);  // lim <= 31
+    return c ? __ffs((int)c) - 1 : -1;
+  } else {
+    const int l0 = min(lim, 64);
+    const uint64_t c0 = ~L.done.lo & (l0 == 64 ? ~0ull : ((1ull << l0) - 1ull));
+    if (c0) return __ffsll((long long)c0) - 1;
+    if constexpr (W == 4) {
+      if (lim > 64) {
+        const uint64_t c1 = ~L.done.hi & ((1ull << (lim - 64)) - 1ull);
+        if (c1) return 64 + __ffsll((long long)c1) - 1;
+      }
     }
+    return -1;
   }
-  return -1;
 }
 
 template <int W>
 __device__ __forceinline__ void flags_set(SmemList<W>& L, int pos) {
-  if (W == 1 || pos < 64)
-    L.done[0] |= 1ull << pos;
-  else
-    L.done[W - 1] |= 1ull << (pos - 64);
+  if constexpr (W == 1) {
+    L.done.lo |= 1u << pos;
+  } else if constexpr (W == 2) {
+    L.done.lo |= 1ull << pos;
+  } else {
+    if (pos < 64)
+      L.done.lo |= 1ull << pos;
+    else
+      L.done.hi |= 1ull << (pos - 64);
+  }
 }
 
 // Inserts key c if not present; caller checks c < L.worst.
@@ -627,7 +649,8 @@ __device__ __forceinline__ bool strictly_closer(float qx, float qy, float qz, fl
 template <int W>
 __device__ __forceinline__ void knn_query_smem(const CloudDev& C, float qx, float qy, float qz,
                                                int k, int m, uint64_t* col,
-                                               int32_t* __restrict__ oi, float* __restrict__ od) {
+                                               int32_t* __restrict__ out_idx,
+                                               float* __restrict__ out_d2, int32_t row) {
   // an entry past the end of a row: rank bits 0x7fffffff, never < m
   const float4 kNone = make_float4(0.f, 0.f, 0.f, __int_as_float(0x7fffffff));
   SmemList<W> L;
@@ -673,6 +696,10 @@ __device__ __forceinline__ void knn_query_smem(const CloudDev& C, float qx, floa
     end = rr.y;
     next = e < end ? __ldg(C.ent + e) : kNone;
   }
+  // the output row is addressed only now, from its 32-bit index (fewer
+  // registers held through the loop)
+  int32_t* oi = out_idx + (int64_t)row * k;
+  float* od = out_d2 + (int64_t)row * k;
   for (int p = 0; p < k; ++p) {
     const bool real = p < L.cnt;
     const uint64_t key = real ? L.col[p * 32] : 0ull;

@@ -118,26 +118,26 @@ __global__ void __launch_bounds__(THREADS, THREADS == 256 ? 5 : 1) knn_plain_sme
   extern __shared__ uint64_t smem_lists[];
   const int warp = (int)(threadIdx.x >> 5), lane = (int)(threadIdx.x & 31u);
   uint64_t* col = smem_lists + (size_t)warp * kcap * 32 + lane;
-  const int64_t stride = (int64_t)gridDim.x * THREADS;
+  // 32-bit query indices (nq < 2^31) keep registers free for residency.
   // Each thread moves on to its next query as soon as it is done with one:
   // nothing makes the warp's lanes wait for each other at query boundaries
   // (a warp-synchronous variant that did was measured 1.3x-1.6x slower).
-  for (int64_t i = (int64_t)blockIdx.x * THREADS + threadIdx.x; i < nq; i += stride) {
-    const int64_t qi = perm ? (int64_t)__ldg(perm + i) : i;
-    const float* qp = q + qi * q_stride;
+  const int32_t n32 = (int32_t)nq;
+  for (int32_t i = (int32_t)(blockIdx.x * THREADS + threadIdx.x); i < n32;
+       i += (int32_t)(gridDim.x * THREADS)) {
+    const int32_t qi = perm ? __ldg(perm + i) : i;
+    const float* qp = q + (int64_t)qi * q_stride;
     const float qx = __ldg(qp), qy = __ldg(qp + 1), qz = __ldg(qp + 2);
     const int m = mq ? __ldg(mq + qi) : m_scalar;
-    int32_t* oi = out_idx + qi * k;
-    float* od = out_d2 + qi * k;
     if (m < 1 || m > C.n) {
       for (int p = 0; p < k; ++p) {
-        oi[p] = -1;
-        od[p] = __int_as_float(0x7f800000);
+        out_idx[(int64_t)qi * k + p] = -1;
+        out_d2[(int64_t)qi * k + p] = __int_as_float(0x7f800000);
       }
       atomicOr(err, 1);
       continue;
     }
-    knn_query_smem<W>(C, qx, qy, qz, k, m, col, oi, od);
+    knn_query_smem<W>(C, qx, qy, qz, k, m, col, out_idx, out_d2, qi);
   }
 }
 
@@ -149,7 +149,7 @@ constexpr size_t smem_bytes(int kcap) {
 
 template <int THREADS, int KMAX>
 cudaError_t run_smem(const CloudDevHost& c, const PlainLaunch& L, cudaStream_t stream) {
-  constexpr int W = KMAX > 64 ? 2 : 1;  // words of expanded flags
+  constexpr int W = KMAX / 32;  // 32-bit words of expanded flags
   const int kcap = L.k;
   const size_t smem = smem_bytes<THREADS>(kcap);
   static std::mutex mu;
