@@ -637,6 +637,20 @@ __device__ __forceinline__ bool strictly_closer(float qx, float qy, float qz, fl
   return sqd64(qx, qy, qz, ps.x, ps.y, ps.z) < sqd64(qx, qy, qz, pc.x, pc.y, pc.z);
 }
 
+// strictly_closer with the current site given by its rank: its coordinates
+// are loaded only when the float32 decision is inside the guard band.
+__device__ __forceinline__ bool strictly_closer_at(const CloudDev& C, float qx, float qy, float qz,
+                                                   float d, float4 ps, float dcur, int cur) {
+  if (dcur >= kTiny) {
+    if (d < dcur * (1.f - kGuard)) return true;
+    if (d > dcur * (1.f + kGuard)) return false;
+  } else if (d > 2.f * kTiny) {
+    return false;
+  }
+  const float4 pc = __ldg(C.pts + cur);
+  return sqd64(qx, qy, qz, ps.x, ps.y, ps.z) < sqd64(qx, qy, qz, pc.x, pc.y, pc.z);
+}
+
 // Algorithms 1 and 2 for one query as one flat loop: each iteration either
 // consumes one successor entry (a descent step while descending, an offer
 // to N while expanding) or moves to the next row (a descent move, the end
@@ -655,10 +669,11 @@ __device__ __forceinline__ void knn_query_smem(const CloudDev& C, float qx, floa
   const float4 kNone = make_float4(0.f, 0.f, 0.f, __int_as_float(0x7fffffff));
   SmemList<W> L;
   slist_init(L, col);
-  float4 pc = __ldg(C.pts);
-  float dcur = sqd32(qx, qy, qz, pc);
+  float dcur = sqd32(qx, qy, qz, __ldg(C.pts));
   slist_insert(L, pack_key(dcur, 0u), k);
-  bool desc = true;
+  // rank of the descent's current site, -1 once the descent is over (its
+  // coordinates are reloaded only for a float64 recheck, which is rare)
+  int cur = 0;
   int2 rr = __ldg(C.rows);
   int e = rr.x, end = rr.y;
   float4 next = e < end ? __ldg(C.ent + e) : kNone;
@@ -670,10 +685,10 @@ __device__ __forceinline__ void knn_query_smem(const CloudDev& C, float qx, floa
       next = e < end ? __ldg(C.ent + e) : kNone;
       const float d = sqd32(qx, qy, qz, ps);
       const uint64_t key = pack_key(d, (uint32_t)s);
-      if (desc) {
-        if (strictly_closer(qx, qy, qz, d, ps, dcur, pc)) {
+      if (cur >= 0) {
+        if (strictly_closer_at(C, qx, qy, qz, d, ps, dcur, cur)) {
           dcur = d;
-          pc = ps;
+          cur = s;
           if (key < L.worst) slist_insert(L, key, k);
           rr = __ldg(C.rows + s);
           e = rr.x;
@@ -686,7 +701,7 @@ __device__ __forceinline__ void knn_query_smem(const CloudDev& C, float qx, floa
       continue;
     }
     // the current row is done: no closer site in it (descent), or fully offered
-    desc = false;
+    cur = -1;
     const int pos = flags_first_clear(L, min(L.cnt, k - 1));
     if (pos < 0) break;
     flags_set(L, pos);
