@@ -105,23 +105,23 @@ __device__ __forceinline__ void serve_item(const ReqDev& R, const Item& w) {
     const float* qp = R.q + qi * R.q_stride;
     const float qx = __ldg(qp), qy = __ldg(qp + 1), qz = __ldg(qp + 2);
     const int m = R.m ? __ldg(R.m + qi) : R.m_scalar;
-    int32_t* oi = R.out_idx + qi * R.k;
-    float* od = R.out_d2 + qi * R.k;
     if (m < 1 || m > C.n) {
-      pad_row(g, R.k, oi, od);
+      pad_row(g, R.k, R.out_idx + qi * R.k, R.out_d2 + qi * R.k);
       if (g.lane == 0) atomicOr(R.err, 1);
       continue;
     }
     QueryCounters qc{0, 0, 0, 0};
-    knn_query<G, S, false>(C, g, qx, qy, qz, R.k, m, oi, od, qc);
+    knn_query<G, S, false>(C, g, qx, qy, qz, R.k, m, R.out_idx, R.out_d2, (int32_t)qi, qc);
   }
 }
 
 // One group variant (lists in registers) per kernel, so that each gets the
 // registers it needs and the occupancy that follows (a single kernel holding
 // every variant behind a switch was held to the largest one's registers).
+// Variants with at most two slots per lane are held to 48 registers (five
+// blocks per SM), as their plain counterparts compile to.
 template <int G, int S>
-__global__ void __launch_bounds__(kThreads) knn_batch_group_kernel(const ReqDev* __restrict__ reqs,
+__global__ void __launch_bounds__(kThreads, S <= 2 ? 5 : (S <= 4 ? 4 : 3)) knn_batch_group_kernel(const ReqDev* __restrict__ reqs,
                                                                    const Item* __restrict__ items,
                                                                    int nitems,
                                                                    int* __restrict__ next,

@@ -182,16 +182,18 @@ struct QueryCounters {
 // One query by one group. m in [1, n]. Writes k results to oi / od.
 template <int G, int S, bool COUNT>
 __device__ __forceinline__ void knn_query(const CloudDev& C, const Grp<G>& g, float qx, float qy,
-                                          float qz, int k, int m, int32_t* __restrict__ oi,
-                                          float* __restrict__ od, QueryCounters& qc) {
+                                          float qz, int k, int m, int32_t* __restrict__ out_idx,
+                                          float* __restrict__ out_d2, int32_t row,
+                                          QueryCounters& qc) {
   const float INF = __int_as_float(0x7f800000);
   TopK<G, S> T;
   topk_init(T);
 
   // ---- Algorithm 1: descent from p_1 (rank 0), collecting transition sites
+  // (the current site is held as a rank; its coordinates are reloaded only
+  // for a float64 recheck)
   int curr = 0;
-  float4 pc = __ldg(C.pts);
-  float dcur = sqd32(qx, qy, qz, pc);
+  float dcur = sqd32(qx, qy, qz, __ldg(C.pts));
   topk_insert(T, g, dcur, 0u, k);
   if (COUNT) {
     qc.coords = 1;
@@ -221,7 +223,10 @@ __device__ __forceinline__ void knn_query(const CloudDev& C, const Grp<G>& g, fl
       uint32_t closer = g.ballot(sure);
       if (g.ballot(maybe)) {
         bool c64 = false;
-        if (maybe) c64 = sqd64(qx, qy, qz, ps.x, ps.y, ps.z) < sqd64(qx, qy, qz, pc.x, pc.y, pc.z);
+        if (maybe) {
+          const float4 pc = __ldg(C.pts + curr);
+          c64 = sqd64(qx, qy, qz, ps.x, ps.y, ps.z) < sqd64(qx, qy, qz, pc.x, pc.y, pc.z);
+        }
         closer |= g.ballot(c64);
       }
       const uint32_t stop = g.ballot(valid && !inr);
@@ -234,9 +239,6 @@ __device__ __forceinline__ void knn_query(const CloudDev& C, const Grp<G>& g, fl
         }
         curr = g.shfl(s, w);
         dcur = g.shfl(d, w);
-        pc.x = g.shfl(ps.x, w);
-        pc.y = g.shfl(ps.y, w);
-        pc.z = g.shfl(ps.z, w);
         topk_insert(T, g, dcur, (uint32_t)curr, k);
         moved = true;
         break;
@@ -317,6 +319,8 @@ __device__ __forceinline__ void knn_query(const CloudDev& C, const Grp<G>& g, fl
   }
 
   // ---- output: sorted (d, rank), padded with (-1, +inf)
+  int32_t* oi = out_idx + (int64_t)row * k;
+  float* od = out_d2 + (int64_t)row * k;
 #pragma unroll
   for (int s = 0; s < S; ++s) {
     const int p = s * G + (int)g.lane;

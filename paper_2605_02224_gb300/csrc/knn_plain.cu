@@ -26,15 +26,13 @@ __global__ void __launch_bounds__(kThreads) knn_plain_kernel(
     const float* qp = q + qi * q_stride;
     const float qx = __ldg(qp), qy = __ldg(qp + 1), qz = __ldg(qp + 2);
     const int m = mq ? __ldg(mq + qi) : m_scalar;
-    int32_t* oi = out_idx + qi * k;
-    float* od = out_d2 + qi * k;
     if (m < 1 || m > C.n) {
-      pad_row(g, k, oi, od);
+      pad_row(g, k, out_idx + qi * k, out_d2 + qi * k);
       if (g.lane == 0) atomicOr(err, 1);
       continue;
     }
     QueryCounters qc{0, 0, 0, 0};
-    knn_query<G, S, COUNT>(C, g, qx, qy, qz, k, m, oi, od, qc);
+    knn_query<G, S, COUNT>(C, g, qx, qy, qz, k, m, out_idx, out_d2, (int32_t)qi, qc);
     if (COUNT && g.lane == 0) {
       int32_t* c = counters + 4 * qi;
       c[0] = qc.rows;
