@@ -244,7 +244,15 @@ mknn_status mknn_cloud_append(mknn_cloud* c, const float* xyz, int64_t count,
     c->order.reserve((size_t)n_new);
     for (int64_t i = n_old; i < n_new; ++i) c->order.push_back(i);
     std::string err;
-    if (!c->inc->append(c->xyz.data(), n_new, &added, &err)) return afail(MKNN_EINVAL, err);
+    if (!c->inc->append(c->xyz.data(), n_new, &added, &err)) {
+      // the triangulation cannot be rolled back: the cloud keeps its old
+      // points, table and device copy, and takes no more appends
+      c->xyz.resize((size_t)(3 * n_old));
+      c->order.resize((size_t)n_old);
+      c->inc.reset();
+      return afail(MKNN_EINVAL, err + " (the cloud keeps its previous points and can no "
+                                      "longer be appended to)");
+    }
     c->n = n_new;
     c->csr_stale.store(true);
   } catch (const std::bad_alloc&) {
