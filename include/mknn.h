@@ -142,8 +142,9 @@ mknn_status mknn_cloud_upload(mknn_cloud* cloud, mknn_stream_t stream);
  * before it must be recreated (mknn_batch_run returns EINVAL), and a cloud
  * held by a server cannot be appended to (EBUSY).
  * Errors: EINVAL (not dynamic, NULL, non-finite coordinate, n would exceed
- * 2^31 - 16), EBUSY, ENOMEM, ECUDA. A failure inside the insertion itself
- * leaves the cloud as it was before the call, no longer dynamic. */
+ * 2^31 - 16, an earlier append failed), EBUSY, ENOMEM, ECUDA. A failure
+ * inside the insertion itself leaves the cloud's points and table as they
+ * were before the call, and the cloud takes no further appends. */
 mknn_status mknn_cloud_append(mknn_cloud* cloud, const float* xyz, int64_t count,
                               mknn_stream_t stream);
 

@@ -69,6 +69,23 @@ struct Lists {
     len.assign(n, 0);
     pool.reserve((size_t)n + 16);
   }
+  void pop(int32_t i) {  // removes row i's last entry (undoing an append)
+    int32_t t = tail[i];
+    if (t < 0) return;
+    pool[t].cnt--;
+    len[i]--;
+    total--;
+    if (pool[t].cnt == 0) {  // unlink the emptied block (it stays unused in the pool)
+      if (head[i] == t) {
+        head[i] = tail[i] = -1;
+      } else {
+        int32_t b = head[i];
+        while (pool[b].next != t) b = pool[b].next;
+        pool[b].next = -1;
+        tail[i] = b;
+      }
+    }
+  }
   void grow(int64_t n) {  // rows for new ranks, empty
     head.resize(n, -1);
     tail.resize(n, -1);
@@ -123,7 +140,7 @@ class Builder {
       for (int q = 0; q < L_.pool[bk].cnt; ++q, ++at)
         if (at >= from) out->push_back(L_.pool[bk].e[q]);
   }
-  bool has_tetrahedron() const { return tet_made_; }
+  bool has_tetrahedron() const { return tet_made_ && !broken_; }
   const BuildStats& stats() const { return st_; }
 
  private:
@@ -180,6 +197,7 @@ class Builder {
   const float* X_;
   int32_t n_;
   bool tet_made_ = false;
+  bool broken_ = false;  // an append failed: lists rolled back, no more appends
   std::vector<std::pair<int32_t, int32_t>>* added_ = nullptr;
   std::vector<int32_t> V_, N_;
   std::vector<uint32_t> mark_;
@@ -474,9 +492,22 @@ bool Builder::append(const float* xyz, int32_t n_new,
   twin_.resize(n_new);
   for (int32_t i = n_old; i < n_new; ++i) twin_[i] = i;
   added_ = added;
+  const size_t added0 = added ? added->size() : 0;
   bool ok = true;
   for (int32_t j = n_old; j < n_new && ok; ++j) ok = insert_rank(j, err);
   added_ = nullptr;
+  if (!ok) {
+    // the triangulation keeps the points inserted so far, but the lists go
+    // back to the ranks before this call; no further appends are taken
+    if (added) {
+      for (size_t a = added->size(); a > added0; --a) L_.pop((*added)[a - 1].first);
+      added->resize(added0);
+    }
+    n_ = n_old;
+    L_.longest = 0;
+    for (int32_t i = 0; i < n_old; ++i) L_.longest = std::max<int64_t>(L_.longest, L_.len[i]);
+    broken_ = true;
+  }
   st_.n = n_;
   st_.entries = L_.total;
   return ok;

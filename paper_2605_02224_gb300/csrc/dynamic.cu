@@ -228,6 +228,8 @@ mknn_status mknn_cloud_append(mknn_cloud* c, const float* xyz, int64_t count,
                               mknn_stream_t stream) {
   if (!c) return afail(MKNN_EINVAL, "cloud is NULL");
   if (!c->inc) return afail(MKNN_EINVAL, "the cloud was not built with the dynamic option");
+  if (!c->inc->can_append())
+    return afail(MKNN_EINVAL, "an earlier append failed: the cloud takes no more appends");
   if (count < 0) return afail(MKNN_EINVAL, "count < 0");
   if (count == 0) return MKNN_OK;
   if (!xyz) return afail(MKNN_EINVAL, "xyz is NULL");
@@ -245,11 +247,10 @@ mknn_status mknn_cloud_append(mknn_cloud* c, const float* xyz, int64_t count,
     for (int64_t i = n_old; i < n_new; ++i) c->order.push_back(i);
     std::string err;
     if (!c->inc->append(c->xyz.data(), n_new, &added, &err)) {
-      // the triangulation cannot be rolled back: the cloud keeps its old
-      // points, table and device copy, and takes no more appends
+      // the lists were rolled back: the cloud keeps its old points, table
+      // and device copy, and takes no more appends
       c->xyz.resize((size_t)(3 * n_old));
       c->order.resize((size_t)n_old);
-      c->inc.reset();
       return afail(MKNN_EINVAL, err + " (the cloud keeps its previous points and can no "
                                       "longer be appended to)");
     }
