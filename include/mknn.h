@@ -297,7 +297,7 @@ mknn_status mknn_knn_host(const mknn_cloud* cloud, const float* q, int64_t nq, i
  * memory it may use (so an allocation would fail), or a latency-bound
  * loop that cannot afford the synchronisation cudaMalloc/cudaFree can
  * cause. Its scratch is a fixed device array inside the library
- * (9 MiB + 1.5 KiB) that every GPU using this entry point holds until the
+ * (9 MiB + 1.75 KiB) that every GPU using this entry point holds until the
  * process exits.
  *   Arguments, layout, results and errors are those of mknn_knn, except:
  *   nq must be at most mknn_knn_noalloc_max_queries() (2^20); larger nq

@@ -52,9 +52,10 @@ constexpr int kSortBits = 6;
 constexpr int kSortCells = 1 << (3 * kSortBits);
 constexpr int kSortTile = 1024;                       // cells per scan block
 constexpr int kSortTiles = kSortCells / kSortTile;    // 256
-// histogram + tile totals, each 256-byte aligned (the start of a sort workspace)
-constexpr size_t kSortHistBytes =
-    (((size_t)kSortCells * 4 + 255) & ~(size_t)255) + (((size_t)kSortTiles * 4 + 255) & ~(size_t)255);
+// histogram + tile totals + the queries' bounding box, each 256-byte aligned
+// (the start of a sort workspace)
+constexpr size_t kSortHistBytes = (((size_t)kSortCells * 4 + 255) & ~(size_t)255) +
+                                  (((size_t)kSortTiles * 4 + 255) & ~(size_t)255) + 256;
 // Scratch for the histogram and per-query cells (perm not included).
 size_t sort_workspace_bytes(int64_t nq);
 // Writes perm[nq] (processing order).

@@ -9,7 +9,7 @@
 // cell of each query and the processing order) lives in one fixed
 // file-scope device array instead of a library or caller allocation.
 //
-// The array is kScratchBytes (9 MiB + 1.5 KiB) and holds up to
+// The array is kScratchBytes (9 MiB + 1.75 KiB) and holds up to
 // kMaxQueries = 2^20 queries per call. Every GPU that loads this library
 // keeps it until the process exits. All calls on a device share it, so
 // calls whose work overlaps on the GPU (different streams, or different
@@ -29,7 +29,7 @@ namespace mknn {
 namespace {
 
 constexpr int64_t kMaxQueries = int64_t(1) << 20;
-constexpr size_t kHistBytes = kSortHistBytes;  // cell histogram + tile totals: 1 MiB + 1 KiB
+constexpr size_t kHistBytes = kSortHistBytes;  // histogram, tile totals, box: 1 MiB + 1.25 KiB
 constexpr size_t kScratchBytes = kHistBytes + 2 * (size_t)kMaxQueries * 4 + 512;
 // [histogram + tile totals | cells] [order] for kMaxQueries queries must fit
 static_assert(kSortHistBytes + 2 * (((size_t)kMaxQueries * 4 + 255) & ~(size_t)255) <=

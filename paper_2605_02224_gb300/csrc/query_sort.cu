@@ -1,8 +1,9 @@
-// Query locality sort (counting sort by cell in a 64^3 grid, cells in
-// Morton order). Queries that land in the same or neighbouring cells are
-// then processed by neighbouring lanes, warps and blocks, so the successor
-// rows and coordinates they share are found in L1 and L2. The sort only
-// changes the processing order: each query's result goes to its own row.
+// Query locality sort (counting sort by cell in a 64^3 grid over the
+// queries' own bounding box, cells in Morton order). Queries that land in
+// the same or neighbouring cells are then processed by neighbouring lanes,
+// warps and blocks, so the successor rows and coordinates they share are
+// found in L1 and L2. The sort only changes the processing order: each
+// query's result goes to its own row.
 #include "knn_kernels.h"
 
 namespace mknn {
@@ -17,11 +18,59 @@ __device__ __forceinline__ uint32_t spread3(uint32_t v) {  // 6 bits -> every th
   return x;
 }
 
-__global__ void qsort_hist(const float* __restrict__ q, int stride, int64_t nq, float lox,
-                           float loy, float loz, float sx, float sy, float sz,
-                           int32_t* __restrict__ cell, int32_t* __restrict__ hist) {
+// Float <-> unsigned with the same order (for atomic min / max of floats).
+__device__ __forceinline__ uint32_t float_order(float f) {
+  const uint32_t u = __float_as_uint(f);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float order_float(uint32_t u) {
+  return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
+}
+
+// Bounding box of the queries (NaN coordinates skipped) into box[0..5]:
+// minima then maxima in float_order form (set to all-ones / zero first).
+__global__ void qsort_bbox(const float* __restrict__ q, int stride, int64_t nq,
+                           uint32_t* __restrict__ box) {
+  float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  const int64_t step = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nq; i += step) {
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const float v = __ldg(q + i * stride + d);
+      if (v == v) {
+        lo[d] = fminf(lo[d], v);
+        hi[d] = fmaxf(hi[d], v);
+      }
+    }
+  }
+#pragma unroll
+  for (int d = 0; d < 3; ++d)
+    for (int o = 16; o > 0; o >>= 1) {
+      lo[d] = fminf(lo[d], __shfl_xor_sync(0xffffffffu, lo[d], o));
+      hi[d] = fmaxf(hi[d], __shfl_xor_sync(0xffffffffu, hi[d], o));
+    }
+  if ((threadIdx.x & 31u) == 0) {
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      atomicMin(box + d, float_order(lo[d]));
+      atomicMax(box + 3 + d, float_order(hi[d]));
+    }
+  }
+}
+
+__global__ void qsort_hist(const float* __restrict__ q, int stride, int64_t nq,
+                           const uint32_t* __restrict__ box, int32_t* __restrict__ cell,
+                           int32_t* __restrict__ hist) {
   const int64_t step = (int64_t)gridDim.x * blockDim.x;
   const float cmax = (float)((1 << kSortBits) - 1);
+  float lo[3], sc[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    lo[d] = order_float(box[d]);
+    const float ext = order_float(box[3 + d]) - lo[d];
+    sc[d] = ext > 0.f ? (float)(1 << kSortBits) / ext : 0.f;
+  }
+  const float lox = lo[0], loy = lo[1], loz = lo[2], sx = sc[0], sy = sc[1], sz = sc[2];
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nq; i += step) {
     const float* p = q + i * stride;
     const float fx = fminf(fmaxf((__ldg(p) - lox) * sx, 0.f), cmax);
@@ -105,23 +154,21 @@ cudaError_t launch_query_sort(const CloudDevHost& c, const float* q, int32_t q_s
 cudaError_t launch_query_sort_split(const CloudDevHost& c, const float* q, int32_t q_stride,
                                     int64_t nq, void* hist_buf, int32_t* cell, int32_t* perm,
                                     cudaStream_t stream) {
+  (void)c;  // the grid spans the queries' own bounding box
   int32_t* hist = (int32_t*)hist_buf;
   int32_t* tiles = (int32_t*)((char*)hist_buf + align256((size_t)kSortCells * 4));
+  uint32_t* box = (uint32_t*)((char*)tiles + align256((size_t)kSortTiles * 4));
   if (nq == 0) return cudaSuccess;
   cudaError_t e = cudaMemsetAsync(hist, 0, (size_t)kSortCells * 4, stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(box, 0xff, 12, stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(box + 3, 0, 12, stream);
   if (e != cudaSuccess) return e;
-  const float cells = (float)(1 << kSortBits);
-  float s[3];
-  for (int i = 0; i < 3; ++i) {
-    const float ext = c.hi[i] - c.lo[i];
-    s[i] = ext > 0.f ? cells / ext : 0.f;
-  }
   const int threads = 256;
   int64_t blocks = (nq + threads - 1) / threads;
   const int64_t cap = (int64_t)num_sms() * 8;
   if (blocks > cap) blocks = cap;
-  qsort_hist<<<(unsigned)blocks, threads, 0, stream>>>(q, q_stride, nq, c.lo[0], c.lo[1], c.lo[2],
-                                                       s[0], s[1], s[2], cell, hist);
+  qsort_bbox<<<(unsigned)blocks, threads, 0, stream>>>(q, q_stride, nq, box);
+  qsort_hist<<<(unsigned)blocks, threads, 0, stream>>>(q, q_stride, nq, box, cell, hist);
   qsort_scan_tiles<<<kSortTiles, kSortTile, 0, stream>>>(hist, tiles);
   qsort_scan_top<<<1, kSortTiles, 0, stream>>>(tiles);
   qsort_scatter<<<(unsigned)blocks, threads, 0, stream>>>(cell, nq, hist, tiles, perm);
