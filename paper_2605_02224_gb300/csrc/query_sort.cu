@@ -49,12 +49,24 @@ __global__ void qsort_bbox(const float* __restrict__ q, int stride, int64_t nq,
       lo[d] = fminf(lo[d], __shfl_xor_sync(0xffffffffu, lo[d], o));
       hi[d] = fmaxf(hi[d], __shfl_xor_sync(0xffffffffu, hi[d], o));
     }
-  if ((threadIdx.x & 31u) == 0) {
-#pragma unroll
+  // one set of atomics per block, not per warp
+  __shared__ float part[32][6];
+  const int warp = (int)(threadIdx.x >> 5), nwarps = (int)(blockDim.x >> 5);
+  if ((threadIdx.x & 31u) == 0)
     for (int d = 0; d < 3; ++d) {
-      atomicMin(box + d, float_order(lo[d]));
-      atomicMax(box + 3 + d, float_order(hi[d]));
+      part[warp][d] = lo[d];
+      part[warp][3 + d] = hi[d];
     }
+  __syncthreads();
+  if (threadIdx.x < 3) {
+    const int d = (int)threadIdx.x;
+    float a = part[0][d], b = part[0][3 + d];
+    for (int w = 1; w < nwarps; ++w) {
+      a = fminf(a, part[w][d]);
+      b = fmaxf(b, part[w][3 + d]);
+    }
+    atomicMin(box + d, float_order(a));
+    atomicMax(box + 3 + d, float_order(b));
   }
 }
 
