@@ -197,7 +197,9 @@ mknn_status mknn_cloud_load(const char* path, mknn_cloud** out);
 
 /* ------------------------------------------------------------------ query
  * mknn_knn: exact k-NN for a batch of queries (Algorithms 1 and 2, with the
- * prefix bound of Sec. 4.2), one query per group of lanes.
+ * prefix bound of Sec. 4.2): one query per GPU thread with its candidate
+ * list in shared memory, or a group of lanes per query on clouds with very
+ * long successor lists and for launches too small to fill the GPU.
  *   cloud     uploaded cloud.
  *   q         device float32, nq rows of q_stride floats (x, y, z first).
  *   nq        number of queries, 0 <= nq < 2^31.
@@ -222,7 +224,8 @@ typedef struct {
   int32_t lanes;        /* lanes per query: 0 = default, or 1, 4, 8, 16, 32
                            (4 and 8 hold k <= 64; one lane above 64
                            needs placement 2 and no counters) */
-  int32_t sort;         /* query locality sort: 0 = default, 1 = on, -1 = off */
+  int32_t sort;         /* query locality sort: 0 = default (on from 4096
+                           queries), 1 = on, -1 = off */
   int32_t blocks_per_sm;/* 0 = as many as fit */
   int32_t* counters;    /* device int32[4*nq] or NULL: per query rows opened,
                            successor entries read, coordinates read and
@@ -231,17 +234,16 @@ typedef struct {
   size_t workspace_bytes;
   const int32_t* order; /* device int32[nq] processing order (e.g. from
                            mknn_query_order) or NULL; overrides sort */
-  int32_t placement;    /* candidate list of a one-lane query: 0 = default,
-                           1 = registers (each thread walks alone),
-                           2 = shared memory (a warp walks 32 queries'
-                           rows together) */
+  int32_t placement;    /* candidate list of a one-lane query: 0 = default
+                           (2), 1 = registers, 2 = shared memory (sorted
+                           64-bit keys) */
   int32_t reserved[3];
 } mknn_knn_opts;
 
 /* Locality order of a query batch, the one mknn_knn_ex applies when sort
  * is on: queries counting-sorted by the Morton index of their cell in a
- * 64^3 grid over the cloud's bounding box. Changes only the processing
- * order, never a result.
+ * 64^3 grid over the queries' own bounding box. Changes only the
+ * processing order, never a result.
  *   perm_out   device int32[nq]: query indices in processing order.
  *   workspace  device scratch of mknn_query_order_workspace_size(nq) bytes,
  *              or NULL (library-managed, grown on demand).
@@ -314,18 +316,20 @@ mknn_status mknn_knn_noalloc(const mknn_cloud* cloud, const float* q, int64_t nq
 int64_t mknn_knn_noalloc_max_queries(void);
 
 /* Reads and clears the cloud's device error flags (synchronises the
- * device). Bit 0: a per-query m was outside [1, n]. */
+ * device). Bit 0: a per-query m was outside [1, n], or a site rank given to
+ * mknn_knn_sites was outside [0, n). */
 mknn_status mknn_cloud_check(const mknn_cloud* cloud, int32_t* flags);
 
 /* ------------------------------------------------------- batched queries
  * Many requests, each on its own cloud with its own k and m, answered by
- * one persistent kernel launch that drains a device work queue (items of a
- * few rounds of one request's queries). Per request the kernel variant
+ * persistent kernel launches, one per kernel variant present, each draining
+ * its own device work queue (items of a few rounds of one request's
+ * queries). Per request the kernel variant
  * (lanes per query, candidate slots) comes from the tuning table, filled by
  * mknn_batch_tune, or a default. A plan captures its launches (query
  * locality sorts + the persistent kernel) in a CUDA graph and replays it.
  * The paper answers queries one at a time on a CPU (Sec. 5.1); batching
- * many clouds into one launch is this library's GPU form of the same
+ * many clouds into a few launches is this library's GPU form of the same
  * per-query Algorithms 1-2, with identical results. */
 typedef struct {
   const mknn_cloud* cloud; /* uploaded on the current device */
@@ -340,7 +344,7 @@ typedef struct {
 } mknn_batch_req;
 
 typedef struct {
-  int32_t lanes;          /* 0 = tuned per request, else 4, 8, 16 or 32 for all */
+  int32_t lanes;          /* 0 = tuned per request, else 1, 4, 8, 16 or 32 for all */
   int32_t sort;           /* 0 = sort requests with >= 4096 queries, 1 = all, -1 = none */
   int32_t item_rounds;    /* rounds of the group width per work item (0 = 8,
                              fewer for a plan too small to fill the GPU) */
