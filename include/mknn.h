@@ -202,7 +202,7 @@ mknn_status mknn_cloud_load(const char* path, mknn_cloud** out);
  * long successor lists and for launches too small to fill the GPU.
  *   cloud     uploaded cloud.
  *   q         device float32, nq rows of q_stride floats (x, y, z first).
- *   nq        number of queries, 0 <= nq < 2^31.
+ *   nq        number of queries, 0 <= nq < 2^31 - 1.
  *   q_stride  floats per query row, >= 3 (3 = packed xyz, 4 = float4).
  *   k         1 <= k <= MKNN_MAX_K.
  *   m         device int32[nq] per-query prefix bounds, or NULL.
@@ -334,7 +334,7 @@ mknn_status mknn_cloud_check(const mknn_cloud* cloud, int32_t* flags);
 typedef struct {
   const mknn_cloud* cloud; /* uploaded on the current device */
   const float* q;          /* device float32, nq rows of q_stride floats */
-  int64_t nq;
+  int64_t nq;              /* 0 <= nq < 2^31 - 256 */
   int32_t q_stride;        /* >= 3 */
   int32_t k;               /* 1..MKNN_MAX_K */
   const int32_t* m;        /* device int32[nq] or NULL */
@@ -422,7 +422,7 @@ typedef struct {
   int32_t m;                /* prefix bound for every query: 0 = n, else 1..n */
   int32_t reserved;
   const float* q;           /* HOST float32[nq*3], valid until the request is done */
-  int64_t nq;               /* >= 1 */
+  int64_t nq;               /* 1 <= nq < 2^31 - 256 */
   int32_t* out_idx;         /* HOST int32[nq*k], written when done */
   float* out_d2;            /* HOST float32[nq*k] */
 } mknn_request;

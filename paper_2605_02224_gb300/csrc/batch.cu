@@ -452,7 +452,7 @@ mknn_status mknn_batch_create(const mknn_batch_req* reqs, int32_t nreq,
     if (!R.cloud || !R.cloud->d_pts || R.cloud->device != dev)
       return bfail(MKNN_EINVAL, "request " + std::to_string(r) +
                                     ": cloud missing or not uploaded on the current device");
-    if (R.nq < 0 || R.nq >= (int64_t)0x7FFFFFFF || R.q_stride < 3 || R.k < 1 ||
+    if (R.nq < 0 || R.nq >= kRequestQueryLimit || R.q_stride < 3 || R.k < 1 ||
         R.k > MKNN_MAX_K)
       return bfail(MKNN_EINVAL, "request " + std::to_string(r) + ": bad nq, q_stride or k");
     int32_t ms = R.m_scalar;

@@ -26,6 +26,10 @@ struct ReqDev {
   const float4* ent;   // the cloud's successor entries with sites inlined
 };
 
+// Queries per request below this bound: a lane's query index plus its
+// stride within an item (at most 256 queries) then stays below 2^31 - 1.
+constexpr int64_t kRequestQueryLimit = (int64_t)0x7FFFFFFF - 256;
+
 // A contiguous range of one request's queries (in processing order),
 // served by one warp with kernel variant `variant`.
 struct Item {

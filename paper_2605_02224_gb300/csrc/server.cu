@@ -456,7 +456,7 @@ mknn_status mknn_server_submit(mknn_server* s, const mknn_request* r, uint64_t* 
   if (r->cloud < 0 || r->cloud >= (int32_t)s->clouds.size())
     return sfail(MKNN_EINVAL, "unknown cloud id");
   const mknn_cloud* c = s->clouds[r->cloud];
-  if (r->nq < 1 || r->nq >= (int64_t)0x7FFFFFFF || r->k < 1 || r->k > MKNN_MAX_K ||
+  if (r->nq < 1 || r->nq >= kRequestQueryLimit || r->k < 1 || r->k > MKNN_MAX_K ||
       r->m < 0 || r->m > c->n || !r->q || !r->out_idx || !r->out_d2)
     return sfail(MKNN_EINVAL, "bad request (nq, k, m or NULL buffer)");
   const size_t need = request_bytes(r->nq, r->k) + al(kPackFixed) + 4096 + items_bytes(r->nq, 1);

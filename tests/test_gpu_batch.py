@@ -216,3 +216,8 @@ def test_batch_rejects_bad_requests(torch, clouds):
     reqs[1]["k"] = 129
     with pytest.raises(M.MknnError):
         M.mknn_batch_create(reqs)
+    reqs[1]["k"] = 8
+    reqs[1]["nq"] = 2 ** 31 - 256          # a lane's index + 32 must stay in int32
+    with pytest.raises(M.MknnError) as ei:
+        M.mknn_batch_create(reqs)
+    assert ei.value.status == 1
