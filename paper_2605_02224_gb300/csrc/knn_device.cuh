@@ -327,8 +327,8 @@ __device__ __forceinline__ void knn_query(const CloudDev& C, const Grp<G>& g, fl
     if (p < k) {
       const uint32_t rr = T.r[s] & kRankMask;
       const bool real = rr != kRankMask;
-      oi[p] = real ? (int32_t)rr : -1;
-      od[p] = real ? T.d[s] : INF;
+      __stcs(oi + p, real ? (int32_t)rr : -1);
+      __stcs(od + p, real ? T.d[s] : INF);
     }
   }
 }
@@ -716,14 +716,15 @@ __device__ __forceinline__ void knn_query_smem(const CloudDev& C, float qx, floa
     next = e < end ? __ldg(C.ent + e) : kNone;
   }
   // the output row is addressed only now, from its 32-bit index (fewer
-  // registers held through the loop)
+  // registers held through the loop); streaming stores, so that the rows
+  // written do not push successor entries out of L2
   int32_t* oi = out_idx + (int64_t)row * k;
   float* od = out_d2 + (int64_t)row * k;
   for (int p = 0; p < k; ++p) {
     const bool real = p < L.cnt;
     const uint64_t key = real ? L.col[p * 32] : 0ull;
-    oi[p] = real ? (int32_t)(uint32_t)key : -1;
-    od[p] = real ? __uint_as_float((uint32_t)(key >> 32)) : __int_as_float(0x7f800000);
+    __stcs(oi + p, real ? (int32_t)(uint32_t)key : -1);
+    __stcs(od + p, real ? __uint_as_float((uint32_t)(key >> 32)) : __int_as_float(0x7f800000));
   }
 }
 

@@ -127,9 +127,10 @@ __global__ void __launch_bounds__(THREADS, THREADS == 256 ? 5 : 1) knn_plain_sme
   // runs the descent, expansion and output paths one after another.
   const uint32_t n32 = (uint32_t)nq;
   for (uint32_t i = blockIdx.x * THREADS + threadIdx.x; i < n32; i += gridDim.x * THREADS) {
-    const int32_t qi = perm ? __ldg(perm + i) : (int32_t)i;
+    // queries and their order are read once: streaming loads
+    const int32_t qi = perm ? __ldcs(perm + i) : (int32_t)i;
     const float* qp = q + (int64_t)qi * q_stride;
-    const float qx = __ldg(qp), qy = __ldg(qp + 1), qz = __ldg(qp + 2);
+    const float qx = __ldcs(qp), qy = __ldcs(qp + 1), qz = __ldcs(qp + 2);
     const int m = mq ? __ldg(mq + qi) : m_scalar;
     if (m < 1 || m > C.n) {
       for (int p = 0; p < k; ++p) {
