@@ -226,7 +226,11 @@ typedef struct {
                            needs placement 2 and no counters) */
   int32_t sort;         /* query locality sort: 0 = default (on from 4096
                            queries), 1 = on, -1 = off */
-  int32_t blocks_per_sm;/* 0 = as many as fit */
+  int32_t blocks_per_sm;/* 0 = default: one block per 256 queries for the
+                           one-lane kernel (the hardware refills SMs as
+                           blocks end), as many as fit for the others;
+                           > 0 = at most this many resident blocks per SM,
+                           each thread looping over queries */
   int32_t* counters;    /* device int32[4*nq] or NULL: per query rows opened,
                            successor entries read, coordinates read and
                            transition sites (descent moves + 1) */

@@ -178,10 +178,16 @@ cudaError_t run_smem(const CloudDevHost& c, const PlainLaunch& L, cudaStream_t s
     }
     occ = occ_for[kcap];
   }
-  const int per_sm = L.blocks_per_sm > 0 ? std::min(L.blocks_per_sm, occ) : occ;
+  // By default one block per THREADS queries: the block scheduler starts a
+  // new block wherever one ends, so every SM stays full to the end of the
+  // launch. blocks_per_sm > 0 makes the grid persistent instead (that many
+  // resident blocks per SM, each thread looping over queries).
   const int64_t need = (L.nq + THREADS - 1) / THREADS;
-  int64_t blocks = (int64_t)num_sms() * per_sm;
-  if (need < blocks) blocks = need;
+  int64_t blocks = need;
+  if (L.blocks_per_sm > 0) {
+    const int64_t cap = (int64_t)num_sms() * std::min(L.blocks_per_sm, occ);
+    if (cap < blocks) blocks = cap;
+  }
   if (blocks < 1) blocks = 1;
   CloudDev C{(const float4*)c.pts, c.rows, c.succ, c.n, (const float4*)c.ent};
   knn_plain_smem_kernel<THREADS, W><<<(unsigned)blocks, THREADS, smem, stream>>>(
