@@ -31,6 +31,11 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "k-NN queries/sec (k=16, 1M-pt surface, volume queries) + served p50/p99 vs plain"
+
+
+def metric_name(k: int, n: int) -> str:
+    """The headline metric's name for the k and cloud size actually run."""
+    return METRIC.replace("k=16", f"k={k}").replace("1M-pt", f"{n / 1e6:g}M-pt")
 UNIT = "queries/s"
 KERNEL_SOURCES = ["paper_2605_02224_gb300/csrc/knn_device.cuh",
                   "paper_2605_02224_gb300/csrc/knn_plain.cu"]
@@ -210,7 +215,8 @@ def run_reference(args, rank, world):
             total_q += s
     value = float(np.median(rates))
     line = {
-        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "impl": "reference", "metric": metric_name(args.k, args.n), "value": value,
+        "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wl.nq / value,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
@@ -826,7 +832,7 @@ def main():
 
     if rank == 0:
         line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "metric": metric_name(args.k, args.n), "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
@@ -834,7 +840,7 @@ def main():
                 "workload": f"torus R=1 r=0.3 sigma=1e-4, n={wl.n}, {nq} queries uniform in the "
                             f"bbox padded by 0.2, k={k}, m=n",
                 "n": wl.n, "nq": nq, "k": k, "E": st["entries"],
-                "lanes": lanes or 8,
+                "lanes": lanes or 1,  # 0 asks for the library's default: one lane per query
                 "query_order": "input order" if args.no_sort else "64^3 Morton cell counting sort",
                 "l2": "flushed before every timed step (256 MB write, outside the events)",
                 "build_seconds": build_s if build_s is not None else "cached",
