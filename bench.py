@@ -83,6 +83,17 @@ def _peaks():
         return 6800.0, "fallback"
 
 
+def _query_kernel_name(lanes: int, k: int, placement: int) -> str:
+    """The query kernel a plain launch with these options runs (its default:
+    one lane per query with the list in shared memory)."""
+    if lanes in (0, 1) and placement in (0, 2):
+        threads, words = (256, 1) if k <= 32 else ((128, 2) if k <= 64 else (64, 4))
+        return f"knn_plain_smem_kernel<{threads}, {words}>"
+    if lanes in (0, 1):
+        return "knn_plain_thread_kernel"
+    return f"knn_plain_kernel<{lanes}, S>"
+
+
 def _kernel_hash():
     h = hashlib.sha1()
     for p in KERNEL_SOURCES:
@@ -317,6 +328,22 @@ def serving_section(args, M, torch):
     }
 
 
+# (lanes, slots per lane) of the persistent kernels, as the library's plans pick them
+_PLAN_VARIANTS = [(4, 1), (4, 2), (4, 4), (8, 1), (8, 2), (8, 4), (8, 8), (16, 1), (16, 2),
+                  (16, 4), (32, 1), (32, 2), (1, 64), (16, 8), (32, 4), (1, 128)]
+
+
+def _plan_launches(lanes, reqs) -> int:
+    """Kernels one plan replay launches: the locality sort's five per request
+    of at least 4096 queries, and one persistent kernel per variant present
+    (the fewest slots per lane that hold the request's k)."""
+    variants = set()
+    for g, r in zip(lanes.tolist(), reqs):
+        fits = [v for v in _PLAN_VARIANTS if v[0] == g and v[0] * v[1] >= r["k"]]
+        variants.add(min(fits, key=lambda v: v[1]))
+    return len(variants) + 5 * sum(1 for r in reqs if r["nq"] >= 4096)
+
+
 def batch_workload(args, M, torch):
     """Batching workload: 64 clouds (log-uniform 10k-2M sites, mixed
     surfaces), 2n queries per cloud, k from {1,4,8,16,32}; one persistent
@@ -384,7 +411,7 @@ def batch_workload(args, M, torch):
                    "build_seconds_max": build_s if build_s is not None else "cached"},
         "plain_one_launch_per_cloud": {"value": nq / (ms_plain / 1e3), "ms_per_step": ms_plain},
         "results_identical": same,
-        "gpu_launches": (1 + 4 * len(reqs)) * args.steps,
+        "gpu_launches": _plan_launches(lanes, reqs) * args.steps,
     }
     print(json.dumps(line), flush=True)
 
@@ -849,7 +876,8 @@ def main():
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)",
-                         "kernel": "knn_plain_kernel", "kernel_ms": kern_s * 1e3,
+                         "kernel": _query_kernel_name(lanes, k, args.placement),
+                         "kernel_ms": kern_s * 1e3,
                          "alg_bytes_per_launch": alg_bytes,
                          "alg_bytes_per_query": alg_bytes / nq,
                          "counts_per_query": {"rows": rows / nq, "entries": entries / nq,
@@ -859,7 +887,9 @@ def main():
             "e2e": {"value": world * nq / e2e_s, "unit": UNIT,
                     "h2d_bytes_per_step": nq * 12, "d2h_bytes_per_step": nq * k * 8,
                     "ms_per_step": e2e_s * 1e3, "matches_device_path": agree},
-            "gpu_launches": (1 if args.no_sort else 5) * args.steps,
+            # per step: the query kernel, and unless --no-sort the locality sort's five
+            # (bounding box, histogram, two scan levels, scatter)
+            "gpu_launches": (1 if args.no_sort else 6) * args.steps,
             "clocks": clk,
             "step_ms": step_ms,
             "serving": serving,
