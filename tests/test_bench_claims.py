@@ -1,0 +1,79 @@
+"""What bench.py claims about a run, checked against the sources it
+describes (CPU only): the metric's name, the query kernel's name, the
+launches per step and per plan replay, and the traffic record's hash check."""
+from __future__ import annotations
+
+import json
+import os
+import re
+
+import numpy as np
+import pytest
+
+import bench
+
+CSRC = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                    "paper_2605_02224_gb300", "csrc")
+
+
+def _read(name):
+    with open(os.path.join(CSRC, name)) as f:
+        return f.read()
+
+
+def test_metric_name_follows_k_and_n():
+    assert bench.metric_name(16, 1_000_000) == bench.METRIC
+    assert "k=4," in bench.metric_name(4, 1_000_000)
+    assert "0.25M-pt" in bench.metric_name(16, 250_000)
+
+
+def test_query_kernel_name_matches_the_dispatch():
+    """The one-lane dispatch picks 256/128/64-thread blocks with 1/2/4 flag
+    words for k up to 32/64/128."""
+    src = _read("knn_plain.cu")
+    assert "if (L.k <= 32) return run_smem<256, 32>" in src
+    assert "if (L.k <= 64) return run_smem<128, 64>" in src
+    assert "return run_smem<64, 128>" in src
+    assert "constexpr int W = KMAX / 32;" in src
+    assert bench._query_kernel_name(0, 16, 0) == "knn_plain_smem_kernel<256, 1>"
+    assert bench._query_kernel_name(0, 33, 0) == "knn_plain_smem_kernel<128, 2>"
+    assert bench._query_kernel_name(1, 128, 2) == "knn_plain_smem_kernel<64, 4>"
+    assert bench._query_kernel_name(1, 16, 1) == "knn_plain_thread_kernel"
+    assert bench._query_kernel_name(8, 16, 0).startswith("knn_plain_kernel<8")
+
+
+def test_sort_launches_five_kernels():
+    """A sorted step is the sort's five kernels plus the query kernel."""
+    src = _read("query_sort.cu")
+    body = src[src.index("cudaError_t launch_query_sort_split("):]
+    assert len(re.findall(r"<<<", body)) == 5
+
+
+def test_plan_variant_table_matches_the_library():
+    src = _read("batch.cu")
+    init = src[src.index("constexpr VariantDesc kVariants[] = {"):]
+    init = init[:init.index("};")]
+    table = [(int(a), int(b)) for a, b in re.findall(r"\{(\d+),\s*(\d+)\}", init)]
+    assert table == bench._PLAN_VARIANTS
+    assert "reqs[r].nq < (o.sort > 0 ? 1 : 4096)" in src
+
+
+def test_plan_launch_count():
+    reqs = [dict(k=k, nq=nq) for k, nq in [(16, 20000), (32, 5000), (1, 100), (8, 3_000_000),
+                                          (100, 9000)]]
+    lanes = np.array([1, 32, 1, 1, 32])
+    # variants (1, 64) and (32, 1), (32, 4); four requests of >= 4096 queries
+    assert bench._plan_launches(lanes, reqs) == 3 + 5 * 4
+
+
+def test_traffic_record_is_used_only_for_its_own_sources():
+    assert bench._profiled_traffic("not-a-hash", 1_000_000, 4_000_000) is None
+    path = os.path.join(os.path.dirname(CSRC), "..", "profiles", "knn_plain_torus1m_traffic.json")
+    with open(path) as f:
+        rec = json.load(f)
+    if rec["kernel_hash"] != bench._kernel_hash():
+        pytest.skip("kernel sources changed since the record was taken")
+    got = bench._profiled_traffic(rec["kernel_hash"], 1_000_000, 4_000_000)
+    assert got == pytest.approx(rec["dram_bytes_per_query"] * 4_000_000)
+    assert got == pytest.approx(rec["dram_bytes_read_per_launch"] +
+                                rec["dram_bytes_write_per_launch"], rel=1e-3)
