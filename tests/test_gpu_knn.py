@@ -132,6 +132,35 @@ def test_prefix_bound_per_query_and_padding():
     c.close()
 
 
+def test_persistent_grid_equals_one_block_per_256_queries():
+    """The one-lane kernel's persistent grid (blocks_per_sm > 0: each thread
+    loops over many queries) gives the same rows, bit for bit, as the
+    default grid of one block per 256 queries, with per-query prefix bounds
+    (some outside [1, n]) and k in every block-size class."""
+    P, _ = W.bumpy_sphere(20000, 31)
+    order = W.permutation(20000, 32)
+    c = built_cloud(P, order, "bumpy20k")
+    c.upload()
+    Pr = P[order]
+    nq = 120_001                                    # a ragged last block
+    Q = np.concatenate([W.box_queries(nq // 2, 36, [-1.3] * 3, [1.3] * 3),
+                        W.near_surface_queries("bumpy", nq - nq // 2, 37)])
+    m = np.clip(np.floor(np.exp(W.uniform(38, 1, nq) * np.log(20000))), 1, 20000)
+    m = m.astype(np.int32)
+    m[7::5000] = 0                                  # invalid bounds: padded rows, flag set
+    for k in (1, 16, 40, 100):
+        base_i, base_d = run_knn(c, Q, k, m, lanes=1, placement=2)
+        for bps in (1, 2):
+            i2, d2 = run_knn(c, Q, k, m, lanes=1, placement=2, blocks_per_sm=bps)
+            assert np.array_equal(i2, base_i) and np.array_equal(d2, base_d), (k, bps)
+        ok_rows = np.flatnonzero(m > 0)
+        parity.check_rows(Pr, Q, k, m, base_i, base_d, rows=ok_rows[::997])
+        bad = np.flatnonzero(m == 0)
+        assert np.all(base_i[bad] == -1) and np.all(np.isinf(base_d[bad]))
+    assert c.check() & 1
+    c.close()
+
+
 def test_hub_rows_all_variants():
     """Four nearly planar patches: a few successor lists hold hundreds to
     thousands of entries (hubs). Every row against the oracle, per-query m
