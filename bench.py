@@ -188,7 +188,11 @@ def _cloud_cache(points, order, tag):
     t0 = time.perf_counter()
     c = Cloud.build(points, order)
     secs = time.perf_counter() - t0
-    c.save(path)
+    # written under a name of this process's own, then renamed into place: ranks
+    # that build the same cloud at once never see (or leave) a half-written file
+    tmp = f"{path}.{os.getpid()}.tmp"
+    c.save(tmp)
+    os.replace(tmp, path)
     return c, secs
 
 

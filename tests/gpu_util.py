@@ -26,7 +26,9 @@ def built_cloud(points: np.ndarray, order: np.ndarray, tag: str = "") -> Cloud:
         except M.MknnError:
             os.remove(path)
     c = Cloud.build(points, order)
-    c.save(path)
+    tmp = f"{path}.{os.getpid()}.tmp"               # complete files only, under any
+    c.save(tmp)                                      # number of concurrent writers
+    os.replace(tmp, path)
     return c
 
 
