@@ -219,7 +219,6 @@ def run_reference(args, rank, world):
     import workloads as W
     wl = W.large_torus(n=args.n, nq=args.nq, k=args.k)
     P = wl.ranked_points()
-    per_step = max(8, int(args.cpu_seconds * 2))   # ~0.5 s per query budgeted below
     rates = []
     t_all = time.perf_counter()
     total_q = 0
