@@ -77,3 +77,31 @@ def test_traffic_record_is_used_only_for_its_own_sources():
     assert got == pytest.approx(rec["dram_bytes_per_query"] * 4_000_000)
     assert got == pytest.approx(rec["dram_bytes_read_per_launch"] +
                                 rec["dram_bytes_write_per_launch"], rel=1e-3)
+
+
+def _cache_worker(seed):
+    import bench as b
+    import workloads as W
+    P, _ = W.sphere(3000, seed)
+    c, _ = b._cloud_cache(P, np.arange(3000), "race")
+    return int(c.stats()["entries"])
+
+
+def test_cloud_cache_survives_concurrent_writers():
+    """Processes that build the same cloud at once leave one complete cache
+    file that loads back to the same table, and no temporary files."""
+    import multiprocessing as mp
+    import workloads as W
+    P, _ = W.sphere(3000, 77)
+    h = bench.hashlib.sha1(np.ascontiguousarray(P).tobytes() +
+                           np.ascontiguousarray(np.arange(3000)).tobytes()).hexdigest()[:16]
+    path = os.path.join("/tmp", "mknn_clouds", f"{h}.mknn")
+    if os.path.exists(path):
+        os.remove(path)
+    with mp.get_context("spawn").Pool(3) as pool:
+        entries = pool.map(_cache_worker, [77, 77, 77])
+    assert len(set(entries)) == 1
+    c, secs = bench._cloud_cache(P, np.arange(3000), "race")
+    assert secs is None and int(c.stats()["entries"]) == entries[0]
+    assert not [f for f in os.listdir(os.path.dirname(path)) if f.startswith(h) and
+                f.endswith(".tmp")]
