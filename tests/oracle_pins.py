@@ -178,6 +178,50 @@ def pin_special_cases(knn_one):
     assert list(r) == [4, 30, 31]
 
 
+# ---------------------------------------------------------- keys_upto pins
+
+def pin_upto_hand_example(keys_upto):
+    """The hand example: dmax exactly on a site's distance includes it, a
+    prefix bound m drops later ranks, keys come out ascending."""
+    h = read_hand()
+    P, q = hand_points()
+    for key, vals in h.items():
+        if not key.startswith("upto_"):
+            continue
+        _, ms, ds = key.split("_")
+        r, D = keys_upto(P, q, int(ms[1:]), float(ds[1:]))
+        assert list(r) == vals, (key, list(r), vals)
+        assert np.array_equal(D, np.array([(HAND_Q - HAND_X[v]) ** 2 for v in vals]))
+
+
+def pin_upto_lattice_ring(keys_upto, L=16, seed=5):
+    """Integer lattice, dmax exactly on a ring value: every lattice point of
+    squared distance <= s among ranks < m, enumerated from offsets, ordered
+    by (distance, rank); m is chosen to cut the outer ring."""
+    P, rank_of = lattice_setup(L, seed)
+    n = P.shape[0]
+    cx, cy, cz = 8, 7, 9
+    q = np.array([cx, cy, cz], np.float32)
+    for s in (0, 1, 2, 3, 5):
+        ring = []
+        for a, b, c in itertools.product(range(-3, 4), repeat=3):
+            d = a * a + b * b + c * c
+            if d <= s:
+                ring.append((float(d), _lattice_rank(rank_of, L, cx + a, cy + b, cz + c)))
+        outer = sorted(r for d, r in ring if d == s)
+        cut = outer[len(outer) // 2] if len(outer) > 1 else n   # drops the later half of ring s
+        for m in (n, cut):
+            want = sorted((d, r) for d, r in ring if r < m)
+            r, D = keys_upto(P, q, m, float(s))
+            assert list(r) == [w[1] for w in want], (s, m)
+            assert np.array_equal(D, np.array([w[0] for w in want]))
+            if m == cut and len(outer) > 1:
+                assert len(want) < len(ring)
+
+
+ALL_UPTO_PINS = [pin_upto_hand_example, pin_upto_lattice_ring]
+
+
 ALL_KNN_PINS = [pin_hand_example, pin_lattice_rings, pin_lattice_cell_centres,
                 pin_sphere_centre, pin_exact_rational, pin_special_cases]
 

@@ -11,6 +11,7 @@ import pytest
 import workloads as W
 from paper_2605_02224_gb300 import Cloud
 from paper_2605_02224_gb300 import mknn as M
+from tests import parity
 
 pytestmark = pytest.mark.gpu
 
@@ -41,6 +42,17 @@ def _alone(clouds, r):
     return c.knn_host(r.queries, r.k, r.m)
 
 
+def _check_against_oracle(wls, r, oi, od, every=50):
+    """Rows 0, every, 2*every, ... of a served request against the float64
+    brute-force oracle on P_{1:m} of its cloud (at least one row per request)."""
+    P = wls[r.cloud].ranked_points()
+    nq = r.queries.shape[0]
+    rows = range(0, nq, every)
+    parity.check_rows(P, r.queries, r.k, np.full(nq, r.m, np.int64), np.asarray(oi),
+                      np.asarray(od), rows=rows)
+    return len(rows)
+
+
 def _pinned(torch, shape, dtype):
     return torch.empty(shape, dtype=dtype).pin_memory()
 
@@ -63,10 +75,13 @@ def test_each_result_equal_alone_and_in_the_mix(torch, resident, plain):
     assert st["p99_ms"] >= st["p50_ms"] > 0
     if not plain:
         assert st["mean_requests_per_launch"] > 1.0     # requests really were batched
+    checked = 0
     for r, (oi, od), t in zip(reqs, outs, tickets):
         assert M.mknn_server_poll(srv, t) == 1
         ai, ad = _alone(cl, r)
         assert np.array_equal(oi, ai) and np.array_equal(od, ad)
+        checked += _check_against_oracle(wls, r, oi, od)
+    assert checked >= len(reqs)
     M.mknn_server_destroy(srv, 60.0)
 
 
@@ -101,6 +116,7 @@ def test_poisson_arrivals_pinned_buffers_overlap(torch, resident):
     for r, (q, oi, od) in zip(reqs, bufs):
         ai, ad = _alone(cl, r)
         assert np.array_equal(oi.numpy(), ai) and np.array_equal(od.numpy(), ad)
+        _check_against_oracle(wls, r, oi.numpy(), od.numpy())
     lat = M.mknn_server_latencies(srv, len(reqs))
     assert lat.shape[0] == len(reqs) and np.all(lat > 0)
     M.mknn_server_destroy(srv, 60.0)

@@ -217,3 +217,43 @@ def test_successor_definition_against_empty_spheres(seed):
                 nb.update((a, b, c))
         got = {i for i in range(j) if j in L[i]}
         assert got == nb, (j, sorted(got), sorted(nb))
+
+
+# ------------------------------------------------------- keys_upto
+
+@pytest.mark.parametrize("pin", pins.ALL_UPTO_PINS, ids=lambda f: f.__name__)
+def test_keys_upto_pins(pin):
+    pin(ok.keys_upto)
+
+
+def _planted_upto(kind):
+    def keys_upto(P, q, m, dmax):
+        mm = P.shape[0] if kind == "ignores_m" else int(m)
+        D = ok.sq_dist64(P[:mm], q)
+        cand = np.nonzero(D < dmax)[0] if kind == "strict" else np.nonzero(D <= dmax)[0]
+        if kind == "rank_order":
+            order = np.argsort(cand, kind="stable")
+        elif kind == "tie_high_rank_first":
+            order = np.lexsort((-cand, D[cand]))
+        else:
+            order = np.lexsort((cand, D[cand]))
+        r = cand[order]
+        return r.astype(np.int64), D[r]
+    return keys_upto
+
+
+@pytest.mark.parametrize("kind", ["strict", "ignores_m", "rank_order", "tie_high_rank_first"])
+def test_keys_upto_planted_mistakes_fail_a_pin(kind):
+    bad = _planted_upto(kind)
+    failed = []
+    for pin in pins.ALL_UPTO_PINS:
+        try:
+            pin(bad)
+        except AssertionError:
+            failed.append(pin.__name__)
+    assert failed, f"planted mistake {kind} passed every keys_upto pin"
+
+
+def test_keys_upto_unplanted_copy_passes():
+    for pin in pins.ALL_UPTO_PINS:
+        pin(_planted_upto("none"))
