@@ -30,6 +30,7 @@
 #include "cloud.h"
 #include "knn_device.cuh"
 #include "knn_kernels.h"
+#include "per_device.h"
 
 namespace mknn {
 
@@ -221,11 +222,11 @@ int choose_lanes(int k, int64_t n, int hub, int64_t nq) {
 
 namespace {
 
-// Largest dynamic shared memory each kernel is launched with; set once.
-std::once_flag g_attr_once;
-cudaError_t g_attr_err = cudaSuccess;
+// Largest dynamic shared memory each kernel is launched with; set once per
+// device (a kernel attribute belongs to one device's context).
+PerDevice<int> g_attr_set;
 
-void set_smem_attributes() {
+cudaError_t set_smem_attributes() {
   cudaError_t e = cudaFuncSetAttribute(knn_batch_smem_kernel<256, 1>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)list_bytes(256, 32));
@@ -237,7 +238,16 @@ void set_smem_attributes() {
     e = cudaFuncSetAttribute(knn_batch_smem_kernel<64, 4>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)list_bytes(64, 128));
-  g_attr_err = e;
+  return e;
+}
+
+cudaError_t ensure_smem_attributes() {
+  return g_attr_set.with(current_device(), cudaErrorInvalidDevice, [](int& done) {
+    if (done) return cudaSuccess;
+    const cudaError_t e = set_smem_attributes();
+    if (e == cudaSuccess) done = 1;
+    return e;
+  });
 }
 
 // The kernel of a variant (the one-lane kernel by its block size).
@@ -268,7 +278,7 @@ const void* variant_kernel(int variant, int threads) {
 }  // namespace
 
 BatchLaunch batch_config(int nitems, int blocks_per_sm, int kcap, int variant) {
-  std::call_once(g_attr_once, set_smem_attributes);
+  ensure_smem_attributes();  // an error shows again at launch
   BatchLaunch b;
   b.variant = variant;
   const bool smem = is_smem_variant(variant);
@@ -292,7 +302,8 @@ BatchLaunch batch_config(int nitems, int blocks_per_sm, int kcap, int variant) {
 cudaError_t launch_batch_kernel(const ReqDev* d_reqs, const Item* d_items, int nitems, int* d_next,
                                 const BatchLaunch& b, cudaStream_t s) {
   if (nitems <= 0) return cudaSuccess;
-  if (g_attr_err != cudaSuccess) return g_attr_err;
+  const cudaError_t ae = ensure_smem_attributes();
+  if (ae != cudaSuccess) return ae;
   const void* fn = variant_kernel(b.variant, b.threads);
   if (!fn) return cudaErrorInvalidValue;
   int kcap = b.kcap;

@@ -132,8 +132,6 @@ cudaError_t scratch_for(cudaStream_t s, size_t bytes, void** out) {
   return cudaSuccess;
 }
 
-constexpr int64_t kSortMinQueries = 4096;
-
 size_t perm_bytes(int64_t nq) { return ((size_t)nq * 4 + 255) & ~(size_t)255; }
 
 // Same-manifold queries: the gathered coordinates (float4) and prefix bounds.

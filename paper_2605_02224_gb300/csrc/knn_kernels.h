@@ -56,6 +56,9 @@ constexpr int kSortTiles = kSortCells / kSortTile;    // 256
 // (the start of a sort workspace)
 constexpr size_t kSortHistBytes = (((size_t)kSortCells * 4 + 255) & ~(size_t)255) +
                                   (((size_t)kSortTiles * 4 + 255) & ~(size_t)255) + 256;
+// Batches smaller than this skip the locality sort by default (its five
+// launches and histogram clear cost more than the order saves).
+constexpr int64_t kSortMinQueries = 4096;
 // Scratch for the histogram and per-query cells (perm not included).
 size_t sort_workspace_bytes(int64_t nq);
 // Writes perm[nq] (processing order).
@@ -71,6 +74,9 @@ int default_lanes(int k);
 int default_placement(int k);
 // Largest k the plain kernels hold with this many lanes per query.
 int plain_max_k(int lanes);
+// The current device's ordinal (-1 if it cannot be read) and its SM count
+// (cached per device).
+int current_device();
 int num_sms();
 
 }  // namespace mknn

@@ -1,10 +1,9 @@
 // The plain query kernel: one cloud, a batch of queries, one group of G
 // lanes per query, grid-stride over the (optionally locality-sorted)
 // query order. Sized to the SM count times the resident blocks per SM.
-#include <mutex>
-
 #include "knn_device.cuh"
 #include "knn_kernels.h"
+#include "per_device.h"
 
 namespace mknn {
 
@@ -80,17 +79,22 @@ __global__ void __launch_bounds__(kThreads) knn_plain_thread_kernel(
 
 template <int K, bool COUNT>
 cudaError_t run_thread(const CloudDevHost& c, const PlainLaunch& L, cudaStream_t stream) {
-  static int occ = -1;
-  static std::mutex mu;
-  {
-    std::lock_guard<std::mutex> lk(mu);
-    if (occ < 0) {
+  static PerDevice<int> occ_of;
+  int occ = 0;
+  const cudaError_t oe = occ_of.with(current_device(), cudaErrorInvalidDevice, [&](int& o) {
+    if (o < 1) {
       cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-          &occ, knn_plain_thread_kernel<K, COUNT>, kThreads, 0);
-      if (e != cudaSuccess) return e;
-      if (occ < 1) occ = 1;
+          &o, knn_plain_thread_kernel<K, COUNT>, kThreads, 0);
+      if (e != cudaSuccess) {
+        o = 0;
+        return e;
+      }
+      if (o < 1) o = 1;
     }
-  }
+    occ = o;
+    return cudaSuccess;
+  });
+  if (oe != cudaSuccess) return oe;
   const int per_sm = L.blocks_per_sm > 0 ? std::min(L.blocks_per_sm, occ) : occ;
   const int64_t need = (L.nq + kThreads - 1) / kThreads;
   int64_t blocks = (int64_t)num_sms() * per_sm;
@@ -155,29 +159,33 @@ cudaError_t run_smem(const CloudDevHost& c, const PlainLaunch& L, cudaStream_t s
   constexpr int W = KMAX / 32;  // 32-bit words of expanded flags
   const int kcap = L.k;
   const size_t smem = smem_bytes<THREADS>(kcap);
-  static std::mutex mu;
-  static bool attr = false;
-  static int occ_for[KMAX + 1] = {};
-  int occ;
-  {
-    std::lock_guard<std::mutex> lk(mu);
-    if (!attr) {
-      // once, at the largest size any k <= KMAX needs
+  // per device: the raised shared-memory limit and the occupancy per kcap
+  struct State {
+    bool attr;
+    int occ_for[KMAX + 1];
+  };
+  static PerDevice<State> state;
+  int occ = 0;
+  const cudaError_t se = state.with(current_device(), cudaErrorInvalidDevice, [&](State& st) {
+    if (!st.attr) {
+      // once per device, at the largest size any k <= KMAX needs
       cudaError_t e = cudaFuncSetAttribute(knn_plain_smem_kernel<THREADS, W>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)smem_bytes<THREADS>(KMAX));
       if (e != cudaSuccess) return e;
-      attr = true;
+      st.attr = true;
     }
-    if (!occ_for[kcap]) {
+    if (!st.occ_for[kcap]) {
       int o = 0;
       cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
           &o, knn_plain_smem_kernel<THREADS, W>, THREADS, smem);
       if (e != cudaSuccess) return e;
-      occ_for[kcap] = o < 1 ? 1 : o;
+      st.occ_for[kcap] = o < 1 ? 1 : o;
     }
-    occ = occ_for[kcap];
-  }
+    occ = st.occ_for[kcap];
+    return cudaSuccess;
+  });
+  if (se != cudaSuccess) return se;
   // By default one block per THREADS queries: the block scheduler starts a
   // new block wherever one ends, so every SM stays full to the end of the
   // launch. blocks_per_sm > 0 makes the grid persistent instead (that many
@@ -211,17 +219,22 @@ cudaError_t pick_thread(const CloudDevHost& c, const PlainLaunch& L, cudaStream_
 
 template <int G, int S, bool COUNT>
 cudaError_t run(const CloudDevHost& c, const PlainLaunch& L, cudaStream_t stream) {
-  static int occ = -1;
-  static std::mutex mu;
-  {
-    std::lock_guard<std::mutex> lk(mu);
-    if (occ < 0) {
+  static PerDevice<int> occ_of;
+  int occ = 0;
+  const cudaError_t oe = occ_of.with(current_device(), cudaErrorInvalidDevice, [&](int& o) {
+    if (o < 1) {
       cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-          &occ, knn_plain_kernel<G, S, COUNT>, kThreads, 0);
-      if (e != cudaSuccess) return e;
-      if (occ < 1) occ = 1;
+          &o, knn_plain_kernel<G, S, COUNT>, kThreads, 0);
+      if (e != cudaSuccess) {
+        o = 0;
+        return e;
+      }
+      if (o < 1) o = 1;
     }
-  }
+    occ = o;
+    return cudaSuccess;
+  });
+  if (oe != cudaSuccess) return oe;
   const int per_sm = L.blocks_per_sm > 0 ? std::min(L.blocks_per_sm, occ) : occ;
   const int64_t need = (L.nq * G + kThreads - 1) / kThreads;
   int64_t blocks = (int64_t)num_sms() * per_sm;
@@ -271,17 +284,28 @@ cudaError_t pick_g(const CloudDevHost& c, const PlainLaunch& L, cudaStream_t str
 
 }  // namespace
 
-int num_sms() {
-  static int sms = -1;
-  static std::mutex mu;
-  std::lock_guard<std::mutex> lk(mu);
-  if (sms < 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
-      sms = 1;
+int current_device() {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return -1;
   }
-  return sms;
+  return dev;
+}
+
+int num_sms() {
+  static PerDevice<int> sms_of;
+  const int dev = current_device();
+  return sms_of.with(dev, 1, [&](int& sms) {
+    if (sms < 1) {
+      if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+          sms < 1) {
+        cudaGetLastError();
+        return 1;  // not cached: asked again next time
+      }
+    }
+    return sms;
+  });
 }
 
 // Measured on the 1M-site torus with 4M box queries: one query per thread

@@ -22,6 +22,7 @@
 #include <string>
 
 #include "../../include/mknn.h"
+#include "batch.h"
 #include "cloud.h"
 #include "knn_kernels.h"
 
@@ -117,14 +118,24 @@ extern "C" mknn_status mknn_knn_noalloc(const mknn_cloud* c, const float* q, int
     set_error(std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
     return MKNN_ECUDA;
   }
-  // layout: [histogram + cells (sort scratch)] [processing order]
-  const size_t sort_bytes = sort_workspace_bytes(nq);
-  int32_t* perm = (int32_t*)((char*)base + align256(sort_bytes));
+  // the kernel variant mknn_knn would take for this cloud and batch size
+  const int lanes = choose_lanes(k, c->n, c->hub_bucket(), nq);
+  if (k > plain_max_k(lanes)) {
+    set_error("k above what the chosen lane width holds");
+    return MKNN_EINVAL;
+  }
   cudaStream_t s = (cudaStream_t)stream;
   const mknn::CloudDevHost cd = c->dev();
-  if ((e = launch_query_sort(cd, q, q_stride, nq, base, perm, s)) != cudaSuccess) {
-    set_error(std::string("query sort launch: ") + cudaGetErrorString(e));
-    return MKNN_ECUDA;
+  // layout: [histogram + cells (sort scratch)] [processing order]; small
+  // batches skip the locality sort, as mknn_knn does
+  int32_t* perm = nullptr;
+  if (nq >= kSortMinQueries) {
+    const size_t sort_bytes = sort_workspace_bytes(nq);
+    perm = (int32_t*)((char*)base + align256(sort_bytes));
+    if ((e = launch_query_sort(cd, q, q_stride, nq, base, perm, s)) != cudaSuccess) {
+      set_error(std::string("query sort launch: ") + cudaGetErrorString(e));
+      return MKNN_ECUDA;
+    }
   }
   PlainLaunch L;
   L.q = q;
@@ -138,7 +149,7 @@ extern "C" mknn_status mknn_knn_noalloc(const mknn_cloud* c, const float* q, int
   L.out_d2 = out_d2;
   L.counters = nullptr;
   L.err = c->d_err;
-  L.lanes = default_lanes(k);
+  L.lanes = lanes;
   L.placement = default_placement(k);
   L.blocks_per_sm = 0;
   if ((e = launch_knn_plain(cd, L, s)) != cudaSuccess) {

@@ -64,6 +64,32 @@ def test_noalloc_matches_knn_on_two_calls_in_a_row(torch_cuda):
     cloud.close()
 
 
+def test_noalloc_at_its_limit_and_on_small_batches(torch_cuda):
+    """A batch of exactly the limit fills the whole scratch array; tiny
+    batches on a cloud with long successor lists take the wide lane
+    variant and skip the locality sort, as mknn_knn does."""
+    torch = torch_cuda
+    P, _ = W.torus(50_000, 71)
+    cloud = Cloud.build(P, W.permutation(50_000, 72)).upload()
+    lo, hi = W.padded_box(P)
+    limit = M.mknn_knn_noalloc_max_queries()
+    Q = W.box_queries(limit, 73, lo, hi)
+    ref_i, ref_d = _run(torch, M.mknn_knn, cloud, Q, 8, None)
+    got_i, got_d = _run(torch, M.mknn_knn_noalloc, cloud, Q, 8, None)
+    assert np.array_equal(got_i, ref_i) and np.array_equal(got_d, ref_d)
+    cloud.close()
+    Ph, _ = W.patches4(30_000, 61)
+    hub = Cloud.build(Ph, W.permutation(30_000, 62)).upload()
+    lo, hi = W.padded_box(Ph)
+    for nq, k in ((1, 16), (100, 33), (4095, 5)):
+        Q = W.box_queries(nq, 74 + nq, lo, hi)
+        ref_i, ref_d = _run(torch, M.mknn_knn, hub, Q, k, None)
+        got_i, got_d = _run(torch, M.mknn_knn_noalloc, hub, Q, k, None)
+        assert np.array_equal(got_i, ref_i) and np.array_equal(got_d, ref_d)
+    assert hub.check() == 0
+    hub.close()
+
+
 def test_noalloc_rejects_batches_above_its_limit(torch_cuda):
     torch = torch_cuda
     wl = W.small_sphere(nq=1)
