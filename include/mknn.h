@@ -437,6 +437,11 @@ typedef struct {
   double qps;               /* completed queries / elapsed_s */
   double p50_ms, p99_ms, mean_ms, max_ms;
   double mean_requests_per_launch;
+  /* GPU time of each phase of a launch, summed over completed launches
+   * (stream time between events; launches on different slots overlap):
+   * host-to-device copies of the queries (and the pack's request table),
+   * kernels (locality sorts + k-NN), device-to-host copies of the results */
+  double h2d_ms, kernel_ms, d2h_ms;
 } mknn_serving_stats;
 
 typedef struct mknn_server mknn_server;
@@ -485,6 +490,17 @@ mknn_status mknn_cloud_validate(const mknn_cloud* cloud, int64_t* bad_orient, in
  * Hilbert curve that MKNN_ORDER_BRIO_HILBERT sorts by (1 <= bits <= 21;
  * 0 otherwise). */
 uint64_t mknn_hilbert_index3(uint32_t x, uint32_t y, uint32_t z, int32_t bits);
+
+/* Read-bandwidth probe: reads `bytes` from the device buffer `buf`
+ * `passes` times with 16-byte loads through L2 (bypassing L1), spread over
+ * every SM, and XORs what it read into *sink (device, 4 bytes). Timed with
+ * events around it, bytes * passes / time is the read bandwidth of the
+ * level that holds buf: L2 for a buffer well below its size, HBM for one
+ * well above. Used to set the L2 roofline of the query kernels (their
+ * working set is mostly L2-resident). buf 16-byte aligned, bytes a non-zero
+ * multiple of 16, passes >= 1; otherwise EINVAL. Asynchronous on stream. */
+mknn_status mknn_read_probe(const void* buf, size_t bytes, int32_t passes, uint32_t* sink,
+                            mknn_stream_t stream);
 
 /* Library version string. */
 const char* mknn_version(void);

@@ -107,6 +107,9 @@ struct Slot {
   cudaStream_t aux = nullptr;    // second branch for packs with both kernel families
   cudaEvent_t fork = nullptr, join = nullptr;
   cudaEvent_t done = nullptr;
+  // phase marks of the current launch (timing events): start, after the
+  // host-to-device copies, after the kernels; `done` follows the copies back
+  cudaEvent_t t0 = nullptr, t_h2d = nullptr, t_kern = nullptr;
   bool busy = false;
   std::vector<uint64_t> tickets;
   size_t off = 0, bytes = 0;
@@ -155,6 +158,7 @@ struct mknn_server {
   int64_t inflight = 0;
   // statistics
   int64_t completed = 0, failed = 0, queries = 0, launches = 0, packed = 0;
+  double h2d_ms = 0, kernel_ms = 0, d2h_ms = 0;  // summed over completed launches
   bool have_first = false;
   Clock::time_point t_first, t_last;
   std::vector<std::pair<uint64_t, double>> lat;  // (ticket, ms)
@@ -190,6 +194,18 @@ void mknn_server::reap_locked() {
       lat.emplace_back(t, std::chrono::duration<double, std::milli>(R.t_done - R.t_submit).count());
       (void)now;
     }
+    if (e == cudaSuccess) {
+      float a = 0, b = 0, c = 0;
+      if (cudaEventElapsedTime(&a, sl.t0, sl.t_h2d) == cudaSuccess &&
+          cudaEventElapsedTime(&b, sl.t_h2d, sl.t_kern) == cudaSuccess &&
+          cudaEventElapsedTime(&c, sl.t_kern, sl.done) == cudaSuccess) {
+        h2d_ms += a;
+        kernel_ms += b;
+        d2h_ms += c;
+      } else {
+        cudaGetLastError();
+      }
+    }
     if (e != cudaSuccess) cudaGetLastError();
     arena.release(sl.off, sl.bytes);
     sl.busy = false;
@@ -204,7 +220,7 @@ void mknn_server::launch(Slot& sl, std::vector<uint64_t>& tickets, size_t off, s
   cudaStream_t s = sl.s;
   char* dbase = d_arena + off;
   char* hbase = h_arena + off;
-  cudaError_t e = cudaSuccess;
+  cudaError_t e = cudaEventRecord(sl.t0, s);
   if (o.plain) {
     // baseline: the request alone through the plain entry point
     ReqRec& R = recs[tickets[0] - 1];
@@ -215,7 +231,8 @@ void mknn_server::launch(Slot& sl, std::vector<uint64_t>& tickets, size_t off, s
       std::memcpy(hbase + R.q_off, q.q, qb);
       src = hbase + R.q_off;
     }
-    e = cudaMemcpyAsync(dbase + R.q_off, src, qb, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dbase + R.q_off, src, qb, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaEventRecord(sl.t_h2d, s);
     mknn_knn_opts ko{};
     ko.lanes = o.lanes;
     ko.workspace = dbase + R.cell_off;
@@ -225,6 +242,7 @@ void mknn_server::launch(Slot& sl, std::vector<uint64_t>& tickets, size_t off, s
                     (int32_t*)(dbase + R.idx_off), (float*)(dbase + R.d2_off), &ko,
                     (mknn_stream_t)s) != MKNN_OK)
       e = cudaErrorLaunchFailure;
+    if (e == cudaSuccess) e = cudaEventRecord(sl.t_kern, s);
     void* di = R.out_pinned ? (void*)q.out_idx : (void*)(hbase + R.idx_off);
     void* dd = R.out_pinned ? (void*)q.out_d2 : (void*)(hbase + R.d2_off);
     if (e == cudaSuccess) e = cudaMemcpyAsync(di, dbase + R.idx_off, nk, cudaMemcpyDeviceToHost, s);
@@ -261,11 +279,7 @@ void mknn_server::launch(Slot& sl, std::vector<uint64_t>& tickets, size_t off, s
         src = hbase + R.q_off;
       }
       if (e == cudaSuccess) e = cudaMemcpyAsync(dbase + R.q_off, src, qb, cudaMemcpyHostToDevice, s);
-      const bool sorted = q.nq >= 4096;
-      if (sorted && e == cudaSuccess)
-        e = launch_query_sort_split(cd, (const float*)(dbase + R.q_off), 3, q.nq, d_hist,
-                                    (int32_t*)(dbase + R.cell_off), (int32_t*)(dbase + R.perm_off),
-                                    s);
+      const bool sorted = q.nq >= kSortMinQueries;
       rd[i] = ReqDev{(const float4*)cd.pts, cd.rows, cd.succ, cd.n, 3,
                      (const float*)(dbase + R.q_off), nullptr,
                      sorted ? (const int32_t*)(dbase + R.perm_off) : nullptr,
@@ -286,12 +300,22 @@ void mknn_server::launch(Slot& sl, std::vector<uint64_t>& tickets, size_t off, s
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(dbase + reqs_off, hbase + reqs_off,
                           items_off - reqs_off + sizeof(Item) * ni, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaEventRecord(sl.t_h2d, s);
+    // the locality sort of each request, then the pack's kernels
+    for (int i = 0; i < nreq && e == cudaSuccess; ++i) {
+      const ReqRec& R = recs[tickets[i] - 1];
+      if (R.r.nq >= kSortMinQueries)
+        e = launch_query_sort_split(clouds[R.r.cloud]->dev(), (const float*)(dbase + R.q_off), 3,
+                                    R.r.nq, d_hist, (int32_t*)(dbase + R.cell_off),
+                                    (int32_t*)(dbase + R.perm_off), s);
+    }
     if (e == cudaSuccess) e = cudaMemsetAsync(d_next, 0, segs.size() * sizeof(int), s);
     // the one-lane kernel on the slot's stream, the group kernels on its
     // second stream, joined before the copies back
     if (e == cudaSuccess)
       e = launch_segments((const ReqDev*)(dbase + reqs_off), (const Item*)(dbase + items_off),
                           d_next, segs, s, sl.aux, sl.fork, sl.join);
+    if (e == cudaSuccess) e = cudaEventRecord(sl.t_kern, s);
     for (int i = 0; i < nreq && e == cudaSuccess; ++i) {
       ReqRec& R = recs[tickets[i] - 1];
       const size_t nk = (size_t)R.r.nq * R.r.k * 4;
@@ -425,7 +449,8 @@ mknn_status mknn_server_create(const mknn_server_opts* opts, mknn_server** out) 
         cudaStreamCreateWithFlags(&sl.aux, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&sl.fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&sl.join, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreate(&sl.done) != cudaSuccess || cudaEventCreate(&sl.t0) != cudaSuccess ||
+        cudaEventCreate(&sl.t_h2d) != cudaSuccess || cudaEventCreate(&sl.t_kern) != cudaSuccess) {
       cudaGetLastError();
       return sfail(MKNN_ECUDA, "stream/event creation failed");
     }
@@ -513,6 +538,9 @@ mknn_status mknn_server_stats(mknn_server* s, mknn_serving_stats* out) {
   st.queries = s->queries;
   st.launches = s->launches;
   st.mean_requests_per_launch = s->launches ? (double)s->packed / s->launches : 0.0;
+  st.h2d_ms = s->h2d_ms;
+  st.kernel_ms = s->kernel_ms;
+  st.d2h_ms = s->d2h_ms;
   if (s->have_first && s->completed > 0)
     st.elapsed_s = std::chrono::duration<double>(s->t_last - s->t_first).count();
   st.qps = st.elapsed_s > 0 ? (double)s->queries / st.elapsed_s : 0.0;
@@ -553,6 +581,7 @@ mknn_status mknn_server_reset_stats(mknn_server* s) {
   if (!s) return sfail(MKNN_EINVAL, "NULL server");
   std::lock_guard<std::mutex> lk(s->mu);
   s->completed = s->failed = s->queries = s->launches = s->packed = 0;
+  s->h2d_ms = s->kernel_ms = s->d2h_ms = 0;
   s->have_first = false;
   s->lat.clear();
   return MKNN_OK;
@@ -576,6 +605,9 @@ mknn_status mknn_server_destroy(mknn_server* s, double timeout_s) {
     cudaEventDestroy(sl.done);
     cudaEventDestroy(sl.fork);
     cudaEventDestroy(sl.join);
+    cudaEventDestroy(sl.t0);
+    cudaEventDestroy(sl.t_h2d);
+    cudaEventDestroy(sl.t_kern);
     cudaStreamDestroy(sl.s);
     cudaStreamDestroy(sl.aux);
   }

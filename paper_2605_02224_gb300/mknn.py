@@ -74,7 +74,8 @@ class mknn_serving_stats(C.Structure):
     _fields_ = [(n, C.c_int64) for n in ("submitted", "completed", "failed", "queries",
                                          "launches")] + \
                [(n, C.c_double) for n in ("elapsed_s", "qps", "p50_ms", "p99_ms", "mean_ms",
-                                          "max_ms", "mean_requests_per_launch")]
+                                          "max_ms", "mean_requests_per_launch", "h2d_ms",
+                                          "kernel_ms", "d2h_ms")]
 
     def as_dict(self):
         return {f[0]: getattr(self, f[0]) for f in self._fields_}
@@ -130,6 +131,7 @@ def _declare(L):
         "mknn_cloud_validate": (i32, [vp, vp, vp]),
         "mknn_knn_noalloc": (i32, [vp, vp, i64, i32, i32, vp, i32, vp, vp, vp]),
         "mknn_knn_noalloc_max_queries": (i64, []),
+        "mknn_read_probe": (i32, [vp, sz, i32, vp, vp]),
         "mknn_batch_create": (i32, [vp, i32, vp, pp]),
         "mknn_batch_run": (i32, [vp, vp]),
         "mknn_batch_info": (i32, [vp, vp, vp, vp]),
@@ -369,6 +371,11 @@ def mknn_knn_noalloc(cloud: int, q, nq: int, q_stride: int, k: int, m, m_scalar:
 
 def mknn_knn_noalloc_max_queries() -> int:
     return int(lib().mknn_knn_noalloc_max_queries())
+
+
+def mknn_read_probe(buf, nbytes: int, passes: int, sink, stream: int = 0):
+    """Reads nbytes of the device buffer `passes` times (read-bandwidth probe)."""
+    _check(lib().mknn_read_probe(_ptr(buf), nbytes, passes, _ptr(sink), stream or None))
 
 
 # ---------------------------------------------------------------- batches

@@ -73,6 +73,7 @@ def test_each_result_equal_alone_and_in_the_mix(torch, resident, plain):
     st = M.mknn_server_stats(srv)
     assert st["completed"] == len(reqs) and st["failed"] == 0
     assert st["p99_ms"] >= st["p50_ms"] > 0
+    assert st["h2d_ms"] > 0 and st["kernel_ms"] > 0 and st["d2h_ms"] > 0
     if not plain:
         assert st["mean_requests_per_launch"] > 1.0     # requests really were batched
     checked = 0
