@@ -2,14 +2,23 @@
 """Exact k-NN queries/sec on the 1M-point torus (4M volume queries, k = 16).
 
 One step = one pass of the query path over the whole batch: the locality
-order of the 4M queries (three small kernels) and the k-NN kernel
+order of the 4M queries (five small kernels) and the k-NN kernel
 (Algorithm 1 descent + Algorithm 2 expansion), inputs resident in HBM.
 L2 is flushed (a 256 MB write) before every timed step, outside the timed
 events. Prints one JSON line (rank 0).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
---impl reference times the float64 brute-force oracle on the host cores
+Beside the headline the default single-GPU run reports, each with its own
+clock samples: the same step without the locality sort, a k sweep
+(k = 4, 32, 100), the prefix workload (4M-point bumpy sphere, 8M queries,
+per-query m), the batching workload (64 clouds, one persistent plan against
+one plain launch per cloud), the serving loop (16 resident clouds, Poisson
+arrivals), an L2 read-bandwidth probe for the roofline, and the CPU
+baselines on the host cores (the float64 oracle on a sample, the kd-tree
+and Algorithms 1-2 on the host).
+
+--impl reference times the float64 brute-force oracle on all host cores
 on a bounded sample of the same workload (the slow reference arm).
 Under torchrun each rank runs the same independent batch on its own GPU
 (weak scaling, no collective on the data path).
@@ -59,7 +68,12 @@ def _args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-sort", action="store_true", help="process queries in input order")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving section")
-    ap.add_argument("--serve-requests", type=int, default=400)
+    ap.add_argument("--serve-requests", type=int, default=2000)
+    ap.add_argument("--scale", type=float, default=1.0,
+                    help="size factor of the prefix, batching and serving workloads (1 = as "
+                         "specified; smaller only for trying the benchmark out)")
+    ap.add_argument("--quick", action="store_true",
+                    help="headline only: no sort ablation, k sweep, prefix, batching or CPU baselines")
     ap.add_argument("--workload", default="torus",
                     choices=["torus", "batch", "prefix", "sites", "dynamic", "sweep", "orders"])
     ap.add_argument("--append-batch", type=int, default=10000,
@@ -88,7 +102,8 @@ def _query_kernel_name(lanes: int, k: int, placement: int) -> str:
     one lane per query with the list in shared memory)."""
     if lanes in (0, 1) and placement in (0, 2):
         threads, words = (256, 1) if k <= 32 else ((128, 2) if k <= 64 else (64, 4))
-        return f"knn_plain_smem_kernel<{threads}, {words}>"
+        kind = 8 if k <= 8 else (16 if k <= 16 else 0)
+        return f"knn_plain_smem_kernel<{threads}, {words}, {kind}>"
     if lanes in (0, 1):
         return "knn_plain_thread_kernel"
     return f"knn_plain_kernel<{lanes}, S>"
@@ -173,6 +188,123 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(self.rows)}
 
 
+def _profile_record(khash: str):
+    """The committed ncu record of the headline kernel (launch-list traffic
+    and the section-set figures), if taken on the current kernel sources."""
+    path = os.path.join(ROOT, "profiles", "knn_plain_torus1m_traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+    except Exception:
+        return None
+    return rec if rec.get("kernel_hash") == khash else None
+
+
+def _clocked(local: int, fn):
+    """Runs fn() with nvidia-smi clock samples taken around it."""
+    ck = Clocks(local)
+    ck.start()
+    time.sleep(0.3)
+    try:
+        out = fn()
+    finally:
+        time.sleep(0.2)
+        clk = ck.stop()
+    return out, clk
+
+
+def _timed_ms(torch, stream, fn, steps: int, warmup: int, flush):
+    """CUDA-event times (ms) of `steps` calls of fn on `stream`, each after
+    an L2 flush outside the events, after max(3, warmup) untimed calls."""
+    for _ in range(max(3, warmup)):
+        fn()
+    torch.cuda.synchronize()
+    ms = []
+    for i in range(steps):
+        flush.fill_(float(i))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    return ms
+
+
+def l2_probe(M, torch, dev, stream):
+    """L2 read bandwidth: a buffer of half the L2 size read 50 times per
+    launch with 16-byte loads through L2 (mknn_read_probe), best of 5."""
+    l2 = int(getattr(torch.cuda.get_device_properties(dev), "L2_cache_size", 0) or 0)
+    if l2 <= 0:
+        return None
+    nbytes = (l2 // 2) // 16 * 16
+    buf = torch.ones(nbytes // 4, dtype=torch.int32, device=dev)
+    sink = torch.zeros(1, dtype=torch.int32, device=dev)
+    s = stream.cuda_stream
+    passes = 50
+    M.mknn_read_probe(buf, nbytes, 2, sink, s)          # bring the buffer into L2
+    best = 0.0
+    for _ in range(5):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        M.mknn_read_probe(buf, nbytes, passes, sink, s)
+        b.record(stream)
+        torch.cuda.synchronize()
+        best = max(best, nbytes * passes / (a.elapsed_time(b) / 1e3) / 1e9)
+    return {"l2_read_gbs": best, "buffer_bytes": nbytes, "l2_bytes": l2, "passes": passes,
+            "how": "mknn_read_probe: 16-byte loads through L2 over a buffer of half the L2 "
+                   "size, 50 passes per launch, best of 5 launches (CUDA events)"}
+
+
+def _alg_bytes(rows, entries, coords, nq, k, extra_per_query=0):
+    """Algorithmic bytes of a launch: 12 B per query (xyz) + 8 per row
+    opened (row bounds) + 4 per successor entry + 12 per site coordinate
+    read + 8 k per query (output), plus extra_per_query (e.g. a prefix
+    bound)."""
+    return (12 + extra_per_query) * nq + 8 * rows + 4 * entries + 12 * coords + 8 * k * nq
+
+
+def _roofline(alg_bytes, kern_ms, nq, l2=None, rec=None, kernel=None, counts=None):
+    peak, kind = _peaks()
+    achieved = alg_bytes / (kern_ms / 1e3) / 1e9
+    out = {"bound": "latency/divergence", "achieved": achieved, "peak": peak, "unit": "GB/s",
+           "frac": achieved / peak,
+           "frac_kind": "effective: algorithmic bytes / kernel time, against the measured HBM "
+                        "copy bandwidth (most of the bytes are served by L1/L2, not DRAM)",
+           "peak_source": f"{kind} hbm_gbs (MEASURED_PEAKS.json)",
+           "l2_peak_gbs": (l2 or {}).get("l2_read_gbs"),
+           "frac_l2": achieved / l2["l2_read_gbs"] if l2 else None,
+           "kernel": kernel, "kernel_ms": kern_ms, "alg_bytes_per_launch": alg_bytes,
+           "alg_bytes_per_query": alg_bytes / nq}
+    if counts is not None:
+        out["counts_per_query"] = counts
+    if rec is not None:
+        out["threads_per_inst"] = rec.get("threads_per_inst")
+        out["issue_active"] = rec.get("issue_active_pct")
+        out["profile_kernel_hash"] = rec.get("kernel_hash")
+    return out
+
+
+def _counts(M, torch, cloud, q, nq, k, m, stream, order=None, sort_flag=0, sites=None):
+    """Per-launch totals of rows opened, entries read, coordinates read and
+    transition sites, from the counting kernel (untimed)."""
+    dev = q.device if sites is None else sites.device
+    idx = torch.empty((nq, k), dtype=torch.int32, device=dev)
+    d2 = torch.empty((nq, k), dtype=torch.float32, device=dev)
+    cnt = torch.zeros((nq, 4), dtype=torch.int32, device=dev)
+    lanes = 32 if k > 64 else 1
+    if sites is not None:
+        M.mknn_knn_sites(cloud.handle, sites, nq, k, m, 0, idx, d2, stream, counters=cnt,
+                         lanes=lanes)
+    else:
+        M.mknn_knn_ex(cloud.handle, q, nq, 3, k, m, 0, idx, d2, stream, order=order,
+                      sort=sort_flag, counters=cnt, lanes=lanes)
+    torch.cuda.synchronize()
+    rows, entries, coords, trans = (int(x) for x in cnt.to(torch.int64).sum(dim=0).cpu().numpy())
+    del idx, d2, cnt
+    return rows, entries, coords, trans
+
+
 def _cloud_cache(points, order, tag):
     from paper_2605_02224_gb300 import Cloud
     d = os.path.join("/tmp", "mknn_clouds")
@@ -196,24 +328,135 @@ def _cloud_cache(points, order, tag):
     return c, secs
 
 
-def _oracle_rate(P, Q, k, seconds: float):
-    """Queries/s of the float64 brute-force oracle (one host thread) on a
-    bounded sample of Q: a short probe sizes the sample to ~`seconds`."""
+_ORACLE_P = None
+
+
+def _oracle_init(P):
+    global _ORACLE_P
+    _ORACLE_P = P
+
+
+def _oracle_noop(_):
+    import oracle.knn  # noqa: F401  (imported once per worker before timing)
+    return 0
+
+
+def _oracle_chunk(args):
     import oracle.knn as ok
+    Q, k = args
+    for q in Q:
+        ok.knn_one(_ORACLE_P, q, k, _ORACLE_P.shape[0])
+    return int(Q.shape[0])
+
+
+class OraclePool:
+    """Host processes that run the float64 brute-force oracle, as it
+    stands, on the points P (a spawn pool, so it is safe after CUDA is
+    initialised; workers are started and have imported the oracle before
+    any timing)."""
+
+    def __init__(self, P, cores: int | None = None):
+        import multiprocessing as mp
+        self.cores = cores or os.cpu_count() or 1
+        self.pool = mp.get_context("spawn").Pool(self.cores, initializer=_oracle_init,
+                                                 initargs=(P,))
+        self.pool.map(_oracle_noop, range(self.cores))
+
+    def rate(self, Q, k, seconds: float):
+        """Queries/s over a bounded sample of Q: the first queries, sized
+        from a short probe to about `seconds` of work on all workers.
+        Returns (rate, queries, seconds)."""
+        probe = 4
+        t0 = time.perf_counter()
+        self.pool.apply(_oracle_chunk, ((Q[:probe], k),))
+        per_q = (time.perf_counter() - t0) / probe
+        s = int(max(2 * self.cores,
+                    min(Q.shape[0] - probe, seconds * self.cores / max(per_q, 1e-6))))
+        chunks = np.array_split(Q[probe:probe + s], 4 * self.cores)
+        t0 = time.perf_counter()
+        done = sum(self.pool.map(_oracle_chunk, [(c, k) for c in chunks if c.shape[0]]))
+        return done / (time.perf_counter() - t0), done, time.perf_counter() - t0
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
+def oracle_rate(P, Q, k, seconds: float, cores: int | None = None):
+    """OraclePool(P).rate(...) in one call. Returns (rate, queries, seconds, cores)."""
+    op = OraclePool(P, cores)
+    try:
+        r, s, dt = op.rate(Q, k, seconds)
+    finally:
+        op.close()
+    return r, s, dt, op.cores
+
+
+def _cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def cpu_baselines(P, rowp, succ, Q, k, oracle_seconds: float, single_sample: int = 100_000):
+    """The CPU baselines on this host's cores, in this run: the float64
+    oracle (all cores, a sample), the project's kd-tree and Algorithms 1-2
+    on the host (all cores on every query; one core on a sample). The
+    kd-tree and the host restatement both process the queries in Morton
+    order (the sort is inside the timing) and compute in float64."""
+    import cpu
+    cpu.build()
+    model = _cpu_model()
+    nq = Q.shape[0]
+    rate, s, dt, cores = oracle_rate(P, Q, k, oracle_seconds)
+    threads = cpu.threads()
+    out = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": f"first {s} queries of the workload, float64 brute force over all "
+                     f"{P.shape[0]} sites, {cores} host processes, {dt:.1f} s",
+           "cpu_model": model, "others": []}
     t0 = time.perf_counter()
-    probe = 8
-    for i in range(probe):
-        ok.knn_one(P, Q[i], k, P.shape[0])
-    per_q = (time.perf_counter() - t0) / probe
-    s = int(max(16, min(Q.shape[0] - probe, seconds / max(per_q, 1e-6))))
-    t0 = time.perf_counter()
-    for i in range(probe, probe + s):
-        ok.knn_one(P, Q[i], k, P.shape[0])
-    dt = time.perf_counter() - t0
-    return s / dt, s, dt
+    tree = cpu.KDTree(P)
+    kd_build = time.perf_counter() - t0
+    ref = None
+    for name, fn in (("kd-tree (exact, prefix-aware, float64)",
+                      lambda QQ, th: tree.knn(QQ, k, threads=th)),
+                     ("Algorithms 1-2 on the host (float64, successor table)",
+                      lambda QQ, th: cpu.dpknn(P, rowp, succ, QQ, k, threads=th))):
+        for th, QQ, label in ((0, Q, f"all {nq} queries"),
+                              (1, Q[:single_sample], f"first {min(nq, single_sample)} queries")):
+            t0 = time.perf_counter()
+            idx, _ = fn(QQ, th)
+            dt = time.perf_counter() - t0
+            entry = {"kind": name, "value": QQ.shape[0] / dt, "unit": UNIT,
+                     "cores": threads if th == 0 else 1,
+                     "sample": f"{label}, Morton order, {dt:.2f} s", "cpu_model": model}
+            if th == 0:
+                if ref is None:
+                    ref = idx
+                else:
+                    entry["same_ranks_as_kd_tree"] = bool(np.array_equal(idx, ref))
+            out["others"].append(entry)
+    out["kd_tree_build_seconds"] = kd_build
+    tree.close()
+    return out
 
 
 def run_reference(args, rank, world):
+    """The reference arm: the oracle as it stands on the host cores, each
+    step a bounded sample of the headline workload's queries."""
     if rank != 0:
         return
     import workloads as W
@@ -222,11 +465,15 @@ def run_reference(args, rank, world):
     rates = []
     t_all = time.perf_counter()
     total_q = 0
+    op = OraclePool(P)
+    cores = op.cores
     for step in range(args.warmup + args.steps):
-        r, s, dt = _oracle_rate(P, wl.queries[step * 64:], wl.k, seconds=args.cpu_seconds / 4)
+        Q = wl.queries[(step * 9973) % max(1, wl.nq - 100000):]
+        r, s, dt = op.rate(Q, wl.k, seconds=args.cpu_seconds / 4)
         if step >= args.warmup:
             rates.append(r)
             total_q += s
+    op.close()
     value = float(np.median(rates))
     line = {
         "impl": "reference", "metric": metric_name(args.k, args.n), "value": value,
@@ -236,9 +483,11 @@ def run_reference(args, rank, world):
         "data": "synthetic",
         "config": {"workload": f"torus R=1 r=0.3 sigma=1e-4, n={wl.n}, {wl.nq} box queries, k={wl.k}",
                    "n": wl.n, "nq": wl.nq, "k": wl.k, "m": "n"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": f"{total_q} queries of the workload over {args.steps} steps "
-                                   f"(float64 brute force, one thread); ms_per_step extrapolated"},
+                                   f"(float64 brute force, {cores} host processes); "
+                                   f"ms_per_step extrapolated to all {wl.nq} queries",
+                         "cpu_model": _cpu_model()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "wall_s": time.perf_counter() - t_all,
     }
@@ -272,16 +521,19 @@ def _build_many(wls, tag):
     return [r[0] for r in res], (max(built) if built else None)
 
 
-def serving_section(args, M, torch):
+def serving_section(args, M, torch, built=None):
     """Serving workload: 16 resident clouds (100k-4M sites, mixed surfaces),
-    Poisson arrivals at 0.5 / 0.8 / 0.95 of the plain path's saturation rate;
-    each request 1..65536 queries, k in 1..64, m in [n/10, n]. The batched
-    server (continuous batching, persistent kernel) against the baseline
-    that runs each request alone with the plain kernel, in arrival order, on
-    one stream. Same request sequence for every run (arrival times scaled)."""
+    Poisson arrivals at 0.5 / 0.8 / 0.95 / 1.5 of the plain path's
+    saturation rate; each request 1..65536 queries, k in 1..64, m in
+    [n/10, n]. The batched server (continuous batching, persistent kernel)
+    against the baseline that runs each request alone with the plain
+    kernel, in arrival order, on one stream. Same request sequence for
+    every run (arrival times scaled). Per load: requests per launch,
+    p50/p99 latency, and the GPU time of each launch phase per request."""
     import workloads as W
-    wls = W.serve_clouds()
-    clouds, build_s = _build_many(wls, "serve")
+    wls, clouds, build_s = built if built is not None else (W.serve_clouds(), None, None)
+    if clouds is None:
+        clouds, build_s = _build_many(wls, "serve")
     for c in clouds:
         c.upload()
     n_req = args.serve_requests
@@ -310,24 +562,37 @@ def serving_section(args, M, torch):
         M.mknn_server_drain(srv, 600.0)
         st = M.mknn_server_stats(srv)
         M.mknn_server_destroy(srv, 60.0)
+        done = max(1, st["completed"])
         return {"qps": st["qps"], "rps": st["completed"] / max(st["elapsed_s"], 1e-9),
                 "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"],
                 "launches": st["launches"],
-                "requests_per_launch": st["mean_requests_per_launch"]}
+                "requests_per_launch": st["mean_requests_per_launch"],
+                "gpu_ms_per_request": {"h2d": st["h2d_ms"] / done,
+                                       "kernel": st["kernel_ms"] / done,
+                                       "d2h": st["d2h_ms"] / done}}
 
-    sat_plain = run(1, None)
-    sat_batched = run(0, None)
-    loads = []
-    for f in (0.5, 0.8, 0.95):
-        rate = f * sat_plain["rps"]
-        loads.append({"offered": f, "rate_rps": rate, "batched": run(0, rate),
-                      "plain": run(1, rate)})
+    def measure():
+        sat_plain = run(1, None)
+        sat_batched = run(0, None)
+        loads = []
+        for f in (0.5, 0.8, 0.95, 1.5):
+            rate = f * sat_plain["rps"]
+            loads.append({"offered": f, "rate_rps": rate, "batched": run(0, rate),
+                          "plain": run(1, rate)})
+        return sat_plain, sat_batched, loads
+
+    (sat_plain, sat_batched, loads), clk = _clocked(torch.cuda.current_device(), measure)
+    del bufs
     return {
         "workload": f"16 resident clouds ({sum(w.n for w in wls)} sites, 100k-4M, mixed "
                     f"surfaces); {n_req} requests, {total_q} queries, Poisson arrivals",
         "build_seconds_max": build_s if build_s is not None else "cached",
         "saturation": {"plain": sat_plain, "batched": sat_batched},
         "loads": loads,
+        "phase_times": "GPU time per request of each launch phase (stream time between "
+                       "events, summed over launches / requests): host-to-device copies, "
+                       "kernels (locality sorts + k-NN), device-to-host copies",
+        "clocks": clk,
     }
 
 
@@ -347,14 +612,17 @@ def _plan_launches(lanes, reqs) -> int:
     return len(variants) + 5 * sum(1 for r in reqs if r["nq"] >= 4096)
 
 
-def batch_workload(args, M, torch):
+def batch_section(args, M, torch, built=None):
     """Batching workload: 64 clouds (log-uniform 10k-2M sites, mixed
-    surfaces), 2n queries per cloud, k from {1,4,8,16,32}; one persistent
-    launch per step (graph replay, autotuned) against one plain launch per
-    cloud in sequence on one stream."""
+    surfaces), 2n queries per cloud, k from {1,4,8,16,32}; the tuned
+    persistent plan (one launch per kernel variant, graph replay) against
+    one plain launch per cloud in sequence on one stream. Per-request
+    latency: a request of the plan completes with the plan; a plain request
+    completes with its own launch (CUDA events after each)."""
     import workloads as W
-    wls = W.batch_clouds()
-    clouds, build_s = _build_many(wls, "batch")
+    wls, clouds, build_s = built if built is not None else (W.batch_clouds(), None, None)
+    if clouds is None:
+        clouds, build_s = _build_many(wls, "batch")
     dev = torch.device("cuda", torch.cuda.current_device())
     reqs = []
     for wl, c in zip(wls, clouds):
@@ -372,59 +640,77 @@ def batch_workload(args, M, torch):
     lanes, items, grid = M.mknn_batch_info(plan, len(reqs))
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
     nq = int(sum(r["nq"] for r in reqs))
-
-    def timed(fn):
-        for _ in range(max(3, args.warmup)):
-            fn()
-        torch.cuda.synchronize()
-        ms = []
-        for i in range(args.steps):
-            flush.fill_(float(i))
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            fn()
-            b.record(stream)
-            torch.cuda.synchronize()
-            ms.append(a.elapsed_time(b))
-        return float(np.mean(ms))
-
-    ms_batch = timed(lambda: M.mknn_batch_run(plan, s))
-    ref = [r["out_idx"].clone() for r in reqs]
+    # algorithmic bytes of one pass over every request (counting kernel, untimed)
+    alg = 0
+    for wl, c, r in zip(wls, clouds, reqs):
+        rows, entries, coords, _ = _counts(M, torch, c, r["q"], r["nq"], r["k"], None, s)
+        alg += _alg_bytes(rows, entries, coords, r["nq"], r["k"])
 
     def plain():
         for r in reqs:
             M.mknn_knn(r["cloud"], r["q"], r["nq"], 3, r["k"], None, 0, r["out_idx"],
                        r["out_d2"], s)
 
-    ms_plain = timed(plain)
-    same = all(torch.equal(a, r["out_idx"]) for a, r in zip(ref, reqs))
+    def measure():
+        ms_batch = _timed_ms(torch, stream, lambda: M.mknn_batch_run(plan, s), args.steps,
+                             args.warmup, flush)
+        ref = [r["out_idx"].clone() for r in reqs]
+        ms_plain = _timed_ms(torch, stream, plain, args.steps, args.warmup, flush)
+        same = all(torch.equal(a, r["out_idx"]) for a, r in zip(ref, reqs))
+        # per-request completion times of the plain sequence (one timed pass)
+        flush.fill_(0.0)
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(len(reqs) + 1)]
+        evs[0].record(stream)
+        for i, r in enumerate(reqs):
+            M.mknn_knn(r["cloud"], r["q"], r["nq"], 3, r["k"], None, 0, r["out_idx"],
+                       r["out_d2"], s)
+            evs[i + 1].record(stream)
+        torch.cuda.synchronize()
+        done_plain = np.array([evs[0].elapsed_time(e) for e in evs[1:]])
+        return ms_batch, ms_plain, same, done_plain
+
+    (ms_batch, ms_plain, same, done_plain), clk = _clocked(torch.cuda.current_device(), measure)
     M.mknn_batch_free(plan)
-    line = {
-        "metric": "batched k-NN queries/sec (64 clouds, one persistent launch, autotuned)",
-        "value": nq / (ms_batch / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_batch, "higher_is_better": True,
-        "data": "synthetic", "dtype": "f32",
-        "config": {"workload": f"64 clouds, {sum(w.n for w in wls)} sites, {nq} queries "
-                               f"(half box, half near-surface), k in {{1,4,8,16,32}}",
-                   "l2": "flushed before every timed step", "items": items, "grid": grid,
+    t_b, t_p = float(np.mean(ms_batch)), float(np.mean(ms_plain))
+    return {
+        "workload": f"64 clouds, {sum(w.n for w in wls)} sites, {nq} queries "
+                    f"(half box, half near-surface), k in {{1,4,8,16,32}}",
+        "value": nq / (t_b / 1e3), "unit": UNIT, "ms_per_step": t_b, "steps": args.steps,
+        "plain_one_launch_per_cloud": {"value": nq / (t_p / 1e3), "ms_per_step": t_p},
+        "speedup_vs_plain": t_p / t_b,
+        "results_identical": bool(same),
+        "latency_ms_per_request": {
+            "plan": {"p50": t_b, "p99": t_b, "note": "every request completes with the plan"},
+            "plain": {"p50": float(np.percentile(done_plain, 50)),
+                      "p99": float(np.percentile(done_plain, 99)),
+                      "note": "completion time of each request in the launch sequence"}},
+        "roofline": _roofline(alg, t_b, nq, l2=args._l2, kernel="knn_batch_* (persistent)"),
+        "config": {"items": items, "grid": grid, "l2": "flushed before every timed step",
                    "lanes_chosen": {str(l): int((lanes == l).sum()) for l in set(lanes.tolist())},
-                   "lanes_by_k": {f"k={w.k}": sorted({int(l) for ww, l in zip(wls, lanes)
-                                                     if ww.k == w.k}) for w in wls},
                    "tune_seconds": tune_s,
                    "build_seconds_max": build_s if build_s is not None else "cached"},
-        "plain_one_launch_per_cloud": {"value": nq / (ms_plain / 1e3), "ms_per_step": ms_plain},
-        "results_identical": same,
-        "gpu_launches": _plan_launches(lanes, reqs) * args.steps,
+        "gpu_launches_per_step": _plan_launches(lanes, reqs),
+        "clocks": clk,
     }
+
+
+def batch_workload(args, M, torch):
+    args._l2 = l2_probe(M, torch, torch.device("cuda", torch.cuda.current_device()),
+                        torch.cuda.current_stream())
+    out = batch_section(args, M, torch)
+    line = {"metric": "batched k-NN queries/sec (64 clouds, one persistent launch, autotuned)",
+            "n_gpus": 1, "warmup": args.warmup, "higher_is_better": True, "data": "synthetic",
+            "dtype": "f32", **out}
     print(json.dumps(line), flush=True)
 
 
-def prefix_workload(args, M, torch):
+def prefix_section(args, M, torch, built=None):
     """Prefix workload: 4M-site bumpy sphere, 8M queries (half volume, half
     near-surface), per-query m log-uniform in [1000, n], k = 10."""
     import workloads as W
-    wl = W.prefix_bumpy()
-    cloud, build_s = _cloud_cache(wl.points, wl.order, f"bumpy{wl.n}")
+    wl, cloud, build_s = built if built is not None else (W.prefix_bumpy(), None, None)
+    if cloud is None:
+        cloud, build_s = _cloud_cache(wl.points, wl.order, f"bumpy{wl.n}")
     cloud.upload()
     dev = torch.device("cuda", torch.cuda.current_device())
     q = torch.from_numpy(wl.queries).to(dev)
@@ -435,39 +721,34 @@ def prefix_workload(args, M, torch):
     stream = torch.cuda.current_stream(dev)
     s = stream.cuda_stream
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
-    lanes = args.lanes or 0
-    for _ in range(max(3, args.warmup)):
-        M.mknn_knn_ex(cloud.handle, q, nq, 3, k, m, 0, idx, d2, s, lanes=lanes)
-    cnt = torch.zeros((nq, 4), dtype=torch.int32, device=dev)
-    M.mknn_knn_ex(cloud.handle, q, nq, 3, k, m, 0, idx, d2, s, counters=cnt,
-                  lanes=32 if k > 64 and lanes in (0, 1) else lanes)
-    torch.cuda.synchronize()
-    rows, entries, coords, trans = (int(x) for x in cnt.to(torch.int64).sum(dim=0).cpu().numpy())
-    alg = 12 * nq + 4 * nq + 8 * rows + 4 * entries + 12 * coords + 8 * k * nq
-    ms = []
-    for i in range(args.steps):
-        flush.fill_(float(i))
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        M.mknn_knn_ex(cloud.handle, q, nq, 3, k, m, 0, idx, d2, s, lanes=lanes)
-        b.record(stream)
-        torch.cuda.synchronize()
-        ms.append(a.elapsed_time(b))
+    rows, entries, coords, trans = _counts(M, torch, cloud, q, nq, k, m, s)
+    alg = _alg_bytes(rows, entries, coords, nq, k, extra_per_query=4)
+    ms, clk = _clocked(dev.index, lambda: _timed_ms(
+        torch, stream, lambda: M.mknn_knn(cloud.handle, q, nq, 3, k, m, 0, idx, d2, s),
+        args.steps, args.warmup, flush))
     t = float(np.mean(ms))
-    peak, kind = _peaks()
-    line = {
-        "metric": "prefix k-NN queries/sec (k=10, 4M-pt bumpy sphere, per-query m)",
-        "value": nq / (t / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": t, "higher_is_better": True, "data": "synthetic",
-        "dtype": "f32",
-        "config": {"workload": f"bumpy sphere n={wl.n}, {nq} queries, m log-uniform in "
-                               f"[1000, n], k={k}", "E": cloud.stats()["entries"],
-                   "build_seconds": build_s if build_s is not None else "cached",
-                   "l2": "flushed before every timed step"},
-        "roofline": {"bound": "hbm", "achieved": alg / (t / 1e3) / 1e9, "peak": peak,
-                     "unit": "GB/s", "frac": alg / (t / 1e3) / 1e9 / peak,
-                     "alg_bytes_per_query": alg / nq, "peak_source": kind},
+    del idx, d2, q, m
+    return {
+        "workload": f"bumpy sphere n={wl.n}, {nq} queries (half volume, half near-surface), "
+                    f"m log-uniform in [1000, n] per query, k={k}",
+        "value": nq / (t / 1e3), "unit": UNIT, "ms_per_step": t, "steps": args.steps,
+        "roofline": _roofline(alg, t, nq, l2=args._l2, kernel=_query_kernel_name(0, k, 0),
+                              counts={"rows": rows / nq, "entries": entries / nq,
+                                      "coords": coords / nq, "transitions": trans / nq}),
+        "config": {"E": cloud.stats()["entries"], "l2": "flushed before every timed step",
+                   "step": "locality sort + k-NN kernel (mknn_knn)",
+                   "build_seconds": build_s if build_s is not None else "cached"},
+        "clocks": clk,
     }
+
+
+def prefix_workload(args, M, torch):
+    args._l2 = l2_probe(M, torch, torch.device("cuda", torch.cuda.current_device()),
+                        torch.cuda.current_stream())
+    out = prefix_section(args, M, torch)
+    line = {"metric": "prefix k-NN queries/sec (k=10, 4M-pt bumpy sphere, per-query m)",
+            "n_gpus": 1, "warmup": args.warmup, "higher_is_better": True, "data": "synthetic",
+            "dtype": "f32", **out}
     print(json.dumps(line), flush=True)
 
 
@@ -728,6 +1009,37 @@ def orders_workload(args, M, torch):
     print(json.dumps(line), flush=True)
 
 
+def _start_builds(args):
+    """Generates the extra sections' workloads and builds (or loads) their
+    clouds in background host threads while the headline runs. Returns
+    {section: future of (workloads, clouds, build seconds)}."""
+    from concurrent.futures import ThreadPoolExecutor
+    import workloads as W
+    builders = ThreadPoolExecutor(max_workers=max(1, (os.cpu_count() or 4) - 1))
+    sections = ThreadPoolExecutor(max_workers=3)
+
+    def many(make, tag):
+        wls = make()
+        futs = [builders.submit(_cloud_cache, w.points, w.order, f"{tag}-{w.n}")
+                for w in wls]
+        res = [f.result() for f in futs]
+        built = [r[1] for r in res if r[1] is not None]
+        return wls, [r[0] for r in res], (max(built) if built else None)
+
+    def one(make, tag):
+        wl = make()
+        c, secs = builders.submit(_cloud_cache, wl.points, wl.order, tag).result()
+        return wl, c, secs
+
+    sc = args.scale
+    jobs = {"prefix": sections.submit(one, lambda: W.prefix_bumpy(
+        n=max(2000, int(4_000_000 * sc)), nq=max(1000, int(8_000_000 * sc))), "bumpy")}
+    if not args.no_serve:
+        jobs["serving"] = sections.submit(many, lambda: W.serve_clouds(scale=sc), "serve")
+    jobs["batch"] = sections.submit(many, lambda: W.batch_clouds(scale=sc), "batch")
+    return jobs
+
+
 def main():
     args = _args()
     rank, world, local = _dist_env()
@@ -761,6 +1073,8 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    extras = rank == 0 and world == 1 and not args.quick
+    jobs = _start_builds(args) if extras else {}
 
     wl = W.large_torus(n=args.n, nq=args.nq, k=args.k)
     cloud, build_s = _cloud_cache(wl.points, wl.order, f"torus{wl.n}")
@@ -768,6 +1082,9 @@ def main():
     st = cloud.stats()
     nq, k = wl.nq, wl.k
     dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    sptr = stream.cuda_stream
+    args._l2 = l2_probe(M, torch, dev, stream)
     q = torch.from_numpy(wl.queries).to(dev)
     idx = torch.empty((nq, k), dtype=torch.int32, device=dev)
     d2 = torch.empty((nq, k), dtype=torch.float32, device=dev)
@@ -775,22 +1092,21 @@ def main():
     ws_bytes = M.mknn_query_order_workspace_size(nq)
     ws = torch.empty(max(ws_bytes, 256), dtype=torch.uint8, device=dev)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
-    stream = torch.cuda.current_stream(dev)
-    sptr = stream.cuda_stream
     lanes = args.lanes or 0
 
     order = None if args.no_sort else perm
     sort_flag = -1 if args.no_sort else 0
 
-    def step(ev=None):
+    def step(ev=None, kk=k, oi=idx, od=d2, sorted_=not args.no_sort):
         if ev:
             ev[0].record(stream)
-        if order is not None:
+        if sorted_:
             M.mknn_query_order(cloud.handle, q, nq, 3, perm, ws, ws_bytes, sptr)
         if ev:
             ev[1].record(stream)
-        M.mknn_knn_ex(cloud.handle, q, nq, 3, k, None, 0, idx, d2, sptr, lanes=lanes, order=order,
-                      sort=sort_flag, placement=args.placement, blocks_per_sm=args.blocks_per_sm)
+        M.mknn_knn_ex(cloud.handle, q, nq, 3, kk, None, 0, oi, od, sptr, lanes=lanes,
+                      order=perm if sorted_ else None, sort=0 if sorted_ else -1,
+                      placement=args.placement, blocks_per_sm=args.blocks_per_sm)
         if ev:
             ev[2].record(stream)
 
@@ -799,13 +1115,9 @@ def main():
     torch.cuda.synchronize()
 
     # algorithmic bytes of one launch, from the kernel's own counters (untimed)
-    cnt = torch.zeros((nq, 4), dtype=torch.int32, device=dev)
-    M.mknn_knn_ex(cloud.handle, q, nq, 3, k, None, 0, idx, d2, sptr, order=order,
-                  lanes=32 if k > 64 and lanes in (0, 1) else lanes, sort=sort_flag, counters=cnt)
-    torch.cuda.synchronize()
-    tot = cnt.to(torch.int64).sum(dim=0).cpu().numpy()
-    rows, entries, coords, trans = (int(x) for x in tot)
-    alg_bytes = 12 * nq + 8 * rows + 4 * entries + 12 * coords + 8 * k * nq
+    rows, entries, coords, trans = _counts(M, torch, cloud, q, nq, k, None, sptr, order=order,
+                                           sort_flag=sort_flag)
+    alg_bytes = _alg_bytes(rows, entries, coords, nq, k)
 
     clocks = Clocks(local)
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
@@ -827,38 +1139,82 @@ def main():
         dist.barrier()
     ms_per_step, value = job_rate(total_ms, args.steps, nq, world)
 
-    # end to end through the host-buffer entry point (pinned host memory)
-    qh = torch.from_numpy(wl.queries).pin_memory()
-    oh_i = torch.empty((nq, k), dtype=torch.int32).pin_memory()
-    oh_d = torch.empty((nq, k), dtype=torch.float32).pin_memory()
-    for _ in range(2):
-        M.mknn_knn_host(cloud.handle, qh, k, None, 0, oh_i, oh_d)
-    if dist:
-        dist.barrier()
-    e2e_t = []
-    for _ in range(max(3, args.steps // 2)):
-        t0 = time.perf_counter()
-        M.mknn_knn_host(cloud.handle, qh, k, None, 0, oh_i, oh_d)
-        e2e_t.append(time.perf_counter() - t0)
-    e2e_s = max_over_ranks(float(np.mean(e2e_t)), dist, dev)
-    agree = bool(torch.equal(oh_i, idx.cpu()))
+    def end_to_end():
+        """Queries/s through the host-buffer entry point (pinned host
+        memory, copies inside the timed region), mean over calls."""
+        qh = torch.from_numpy(wl.queries).pin_memory()
+        oh_i = torch.empty((nq, k), dtype=torch.int32).pin_memory()
+        oh_d = torch.empty((nq, k), dtype=torch.float32).pin_memory()
+        for _ in range(2):
+            M.mknn_knn_host(cloud.handle, qh, k, None, 0, oh_i, oh_d)
+        if dist:
+            dist.barrier()
+        e2e_t = []
+        for _ in range(max(3, args.steps // 2)):
+            t0 = time.perf_counter()
+            M.mknn_knn_host(cloud.handle, qh, k, None, 0, oh_i, oh_d)
+            e2e_t.append(time.perf_counter() - t0)
+        return max_over_ranks(float(np.mean(e2e_t)), dist, dev), bool(torch.equal(oh_i, idx.cpu()))
 
     kern_s = float(np.mean(kern_ms)) / 1e3
-    peak, peak_kind = _peaks()
-    achieved = alg_bytes / kern_s / 1e9
     khash = _kernel_hash()
-    traffic = _profiled_traffic(khash, wl.n, nq)
+    rec = _profile_record(khash)
+    roof = _roofline(alg_bytes, kern_s * 1e3, nq, l2=args._l2, rec=rec,
+                     kernel=_query_kernel_name(lanes, k, args.placement),
+                     counts={"rows": rows / nq, "entries": entries / nq, "coords": coords / nq,
+                             "transitions": trans / nq})
+    roof["traffic"] = _profiled_traffic(khash, wl.n, nq)
+    roof["kernel_hash"] = khash
 
-    serving = None
-    if rank == 0 and world == 1 and not args.no_serve:
-        serving = serving_section(args, M, torch)
-
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rate, s, dt = _oracle_rate(wl.ranked_points(), wl.queries, k, args.cpu_seconds)
-        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"first {s} queries of the workload, float64 brute force over all "
-                         f"{wl.n} sites, one host thread, {dt:.1f} s"}
+    no_sort = k_sweep = prefix = batch = serving = cpu = None
+    if not extras:
+        e2e_s, agree = end_to_end()
+    else:
+        # the same step without the locality sort (queries in input order)
+        ms_ns, clk_ns = _clocked(local, lambda: _timed_ms(
+            torch, stream, lambda: step(sorted_=False), args.steps, args.warmup, flush))
+        t_ns = float(np.mean(ms_ns))
+        no_sort = {"value": nq / (t_ns / 1e3), "unit": UNIT, "ms_per_step": t_ns,
+                   "speedup_of_sort": t_ns / ms_per_step,
+                   "roofline": _roofline(alg_bytes, t_ns, nq, l2=args._l2,
+                                         kernel=_query_kernel_name(lanes, k, args.placement)),
+                   "clocks": clk_ns}
+        # k sweep on the same cloud and queries
+        k_sweep = []
+        for kk in (4, 32, 100):
+            oi = torch.empty((nq, kk), dtype=torch.int32, device=dev)
+            od = torch.empty((nq, kk), dtype=torch.float32, device=dev)
+            r_, e_, c_, t_ = _counts(M, torch, cloud, q, nq, kk, None, sptr, order=order,
+                                     sort_flag=sort_flag)
+            ms_k, clk_k = _clocked(local, lambda: _timed_ms(
+                torch, stream, lambda: step(kk=kk, oi=oi, od=od), args.steps, args.warmup,
+                flush))
+            t_k = float(np.mean(ms_k))
+            k_sweep.append({"k": kk, "value": nq / (t_k / 1e3), "unit": UNIT, "ms_per_step": t_k,
+                            "roofline": _roofline(_alg_bytes(r_, e_, c_, nq, kk), t_k, nq,
+                                                  l2=args._l2,
+                                                  kernel=_query_kernel_name(lanes, kk, 0),
+                                                  counts={"rows": r_ / nq, "entries": e_ / nq,
+                                                          "coords": c_ / nq,
+                                                          "transitions": t_ / nq}),
+                            "clocks": clk_k})
+            del oi, od
+        # the host-buffer path after the background builds are done (host
+        # copies and staging are timed, so the host cores should be free)
+        for j in jobs.values():
+            j.result()
+        e2e_s, agree = end_to_end()
+        P_ranked, rowp, succ = cloud.table()
+        del q, idx, d2, perm, ws
+        torch.cuda.empty_cache()
+        prefix = prefix_section(args, M, torch, jobs["prefix"].result())
+        torch.cuda.empty_cache()
+        batch = batch_section(args, M, torch, jobs["batch"].result())
+        torch.cuda.empty_cache()
+        if "serving" in jobs:
+            serving = serving_section(args, M, torch, jobs["serving"].result())
+        if not args.no_cpu_baseline:
+            cpu = cpu_baselines(P_ranked, rowp, succ, wl.queries, k, args.cpu_seconds)
 
     if rank == 0:
         line = {
@@ -876,16 +1232,7 @@ def main():
                 "build_seconds": build_s if build_s is not None else "cached",
                 "parallelism": f"replicas x{world}",
             },
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": traffic,
-                         "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)",
-                         "kernel": _query_kernel_name(lanes, k, args.placement),
-                         "kernel_ms": kern_s * 1e3,
-                         "alg_bytes_per_launch": alg_bytes,
-                         "alg_bytes_per_query": alg_bytes / nq,
-                         "counts_per_query": {"rows": rows / nq, "entries": entries / nq,
-                                              "coords": coords / nq, "transitions": trans / nq},
-                         "kernel_hash": khash},
+            "roofline": roof,
             "cpu_baseline": cpu,
             "e2e": {"value": world * nq / e2e_s, "unit": UNIT,
                     "h2d_bytes_per_step": nq * 12, "d2h_bytes_per_step": nq * k * 8,
@@ -895,6 +1242,11 @@ def main():
             "gpu_launches": (1 if args.no_sort else 6) * args.steps,
             "clocks": clk,
             "step_ms": step_ms,
+            "l2_probe": args._l2,
+            "no_sort": no_sort,
+            "k_sweep": k_sweep,
+            "prefix": prefix,
+            "batch": batch,
             "serving": serving,
         }
         print(json.dumps(line), flush=True)

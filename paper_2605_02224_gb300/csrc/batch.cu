@@ -91,7 +91,7 @@ __device__ __forceinline__ void serve_item_smem(const ReqDev& R, const Item& w, 
       atomicOr(R.err, 1);
       continue;
     }
-    knn_query_smem<W>(C, qx, qy, qz, R.k, m, col, R.out_idx, R.out_d2, (int32_t)qi);
+    knn_query_smem_any<W>(C, qx, qy, qz, R.k, m, col, R.out_idx, R.out_d2, (int32_t)qi);
   }
 }
 
@@ -321,7 +321,7 @@ std::vector<Segment> make_segments(std::vector<Item>& items, int blocks_per_sm,
     int j = i;
     while (j < (int)items.size() && items[j].variant == items[i].variant) ++j;
     int kcap = 0;
-    for (int t = i; t < j; ++t) kcap = std::max(kcap, req_k[items[t].req]);
+    for (int t = i; t < j; ++t) kcap = std::max(kcap, list_slots(req_k[items[t].req]));
     Segment g;
     g.begin = i;
     g.count = j - i;

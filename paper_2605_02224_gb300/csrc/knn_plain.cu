@@ -107,12 +107,15 @@ cudaError_t run_thread(const CloudDevHost& c, const PlainLaunch& L, cudaStream_t
   return cudaGetLastError();
 }
 
-// One query per thread, candidate lists in shared memory (kcap entries per
-// thread, a warp's lists interleaved: thread l of warp w owns column l of
-// the warp's [kcap][32] keys). 256-thread blocks are held to 48 registers
-// (five blocks per SM, no spills): left alone the compiler picks either 40
-// registers with spills or 64, both measured 5%-20% slower.
-template <int THREADS, int W>
+// One query per thread, candidate lists in shared memory (kcap =
+// list_slots(k) entries per thread, a warp's lists interleaved: thread l of
+// warp w owns column l of the warp's [kcap][32] keys). 256-thread blocks are
+// held to 48 registers (five blocks per SM, no spills): left alone the
+// compiler picks either 40 registers with spills or 64, both measured
+// 5%-20% slower, and 4 or 6 blocks per SM were slower too.
+// LK: the list kind (8: SortedList of 8 slots, k <= 8; 16: PermList16,
+// 9 <= k <= 16; 0: SortedList of k slots searched over 32 W).
+template <int THREADS, int W, int LK>
 __global__ void __launch_bounds__(THREADS, THREADS == 256 ? 5 : 1) knn_plain_smem_kernel(
     CloudDev C, const float* __restrict__ q, int q_stride, int64_t nq, int k, int kcap,
     const int32_t* __restrict__ mq, int m_scalar, const int32_t* __restrict__ perm,
@@ -144,7 +147,13 @@ __global__ void __launch_bounds__(THREADS, THREADS == 256 ? 5 : 1) knn_plain_sme
       atomicOr(err, 1);
       continue;
     }
-    knn_query_smem<W>(C, qx, qy, qz, k, m, col, out_idx, out_d2, qi);
+    if constexpr (LK == 8)
+      knn_query_smem<SortedList<8, 1, true>>(C, qx, qy, qz, k, m, col, 8, out_idx, out_d2, qi);
+    else if constexpr (LK == 16)
+      knn_query_smem<PermList16>(C, qx, qy, qz, k, m, col, 16, out_idx, out_d2, qi);
+    else
+      knn_query_smem<SortedList<32 * W, W, false>>(C, qx, qy, qz, k, m, col, k, out_idx, out_d2,
+                                                   qi);
   }
 }
 
@@ -154,10 +163,10 @@ constexpr size_t smem_bytes(int kcap) {
   return (size_t)THREADS * (size_t)kcap * 8;
 }
 
-template <int THREADS, int KMAX>
+template <int THREADS, int KMAX, int LK>
 cudaError_t run_smem(const CloudDevHost& c, const PlainLaunch& L, cudaStream_t stream) {
   constexpr int W = KMAX / 32;  // 32-bit words of expanded flags
-  const int kcap = L.k;
+  const int kcap = list_slots(L.k);
   const size_t smem = smem_bytes<THREADS>(kcap);
   // per device: the raised shared-memory limit and the occupancy per kcap
   struct State {
@@ -169,7 +178,7 @@ cudaError_t run_smem(const CloudDevHost& c, const PlainLaunch& L, cudaStream_t s
   const cudaError_t se = state.with(current_device(), cudaErrorInvalidDevice, [&](State& st) {
     if (!st.attr) {
       // once per device, at the largest size any k <= KMAX needs
-      cudaError_t e = cudaFuncSetAttribute(knn_plain_smem_kernel<THREADS, W>,
+      cudaError_t e = cudaFuncSetAttribute(knn_plain_smem_kernel<THREADS, W, LK>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)smem_bytes<THREADS>(KMAX));
       if (e != cudaSuccess) return e;
@@ -178,7 +187,7 @@ cudaError_t run_smem(const CloudDevHost& c, const PlainLaunch& L, cudaStream_t s
     if (!st.occ_for[kcap]) {
       int o = 0;
       cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-          &o, knn_plain_smem_kernel<THREADS, W>, THREADS, smem);
+          &o, knn_plain_smem_kernel<THREADS, W, LK>, THREADS, smem);
       if (e != cudaSuccess) return e;
       st.occ_for[kcap] = o < 1 ? 1 : o;
     }
@@ -198,7 +207,7 @@ cudaError_t run_smem(const CloudDevHost& c, const PlainLaunch& L, cudaStream_t s
   }
   if (blocks < 1) blocks = 1;
   CloudDev C{(const float4*)c.pts, c.rows, c.succ, c.n, (const float4*)c.ent};
-  knn_plain_smem_kernel<THREADS, W><<<(unsigned)blocks, THREADS, smem, stream>>>(
+  knn_plain_smem_kernel<THREADS, W, LK><<<(unsigned)blocks, THREADS, smem, stream>>>(
       C, L.q, L.q_stride, L.nq, L.k, kcap, L.m, L.m_scalar, L.perm, L.out_idx, L.out_d2, L.err);
   return cudaGetLastError();
 }
@@ -206,9 +215,11 @@ cudaError_t run_smem(const CloudDevHost& c, const PlainLaunch& L, cudaStream_t s
 template <bool COUNT>
 cudaError_t pick_thread(const CloudDevHost& c, const PlainLaunch& L, cudaStream_t stream) {
   if (!COUNT && L.placement == 2) {
-    if (L.k <= 32) return run_smem<256, 32>(c, L, stream);
-    if (L.k <= 64) return run_smem<128, 64>(c, L, stream);
-    return run_smem<64, 128>(c, L, stream);  // 64 KB of lists per block at k = 128
+    if (L.k <= 8) return run_smem<256, 32, 8>(c, L, stream);
+    if (L.k <= 16) return run_smem<256, 32, 16>(c, L, stream);
+    if (L.k <= 32) return run_smem<256, 32, 0>(c, L, stream);
+    if (L.k <= 64) return run_smem<128, 64, 0>(c, L, stream);
+    return run_smem<64, 128, 0>(c, L, stream);  // 64 KB of lists per block at k = 128
   }
   if (L.k > 64) return cudaErrorInvalidValue;  // register lists hold k <= 64
   if (L.k <= 8) return run_thread<8, COUNT>(c, L, stream);

@@ -29,15 +29,20 @@ def test_metric_name_follows_k_and_n():
 
 def test_query_kernel_name_matches_the_dispatch():
     """The one-lane dispatch picks 256/128/64-thread blocks with 1/2/4 flag
-    words for k up to 32/64/128."""
+    words for k up to 32/64/128, and the list kind: 8 slots (k <= 8), the
+    permutation list (k <= 16), k slots above."""
     src = _read("knn_plain.cu")
-    assert "if (L.k <= 32) return run_smem<256, 32>" in src
-    assert "if (L.k <= 64) return run_smem<128, 64>" in src
-    assert "return run_smem<64, 128>" in src
+    assert "if (L.k <= 8) return run_smem<256, 32, 8>" in src
+    assert "if (L.k <= 16) return run_smem<256, 32, 16>" in src
+    assert "if (L.k <= 32) return run_smem<256, 32, 0>" in src
+    assert "if (L.k <= 64) return run_smem<128, 64, 0>" in src
+    assert "return run_smem<64, 128, 0>" in src
     assert "constexpr int W = KMAX / 32;" in src
-    assert bench._query_kernel_name(0, 16, 0) == "knn_plain_smem_kernel<256, 1>"
-    assert bench._query_kernel_name(0, 33, 0) == "knn_plain_smem_kernel<128, 2>"
-    assert bench._query_kernel_name(1, 128, 2) == "knn_plain_smem_kernel<64, 4>"
+    assert bench._query_kernel_name(0, 16, 0) == "knn_plain_smem_kernel<256, 1, 16>"
+    assert bench._query_kernel_name(0, 4, 0) == "knn_plain_smem_kernel<256, 1, 8>"
+    assert bench._query_kernel_name(0, 20, 0) == "knn_plain_smem_kernel<256, 1, 0>"
+    assert bench._query_kernel_name(0, 33, 0) == "knn_plain_smem_kernel<128, 2, 0>"
+    assert bench._query_kernel_name(1, 128, 2) == "knn_plain_smem_kernel<64, 4, 0>"
     assert bench._query_kernel_name(1, 16, 1) == "knn_plain_thread_kernel"
     assert bench._query_kernel_name(8, 16, 0).startswith("knn_plain_kernel<8")
 
@@ -105,3 +110,27 @@ def test_cloud_cache_survives_concurrent_writers():
     assert secs is None and int(c.stats()["entries"]) == entries[0]
     assert not [f for f in os.listdir(os.path.dirname(path)) if f.startswith(h) and
                 f.endswith(".tmp")]
+
+
+def test_algorithmic_bytes_and_roofline_fields():
+    """The byte count per query is 12 (xyz) + 8 per row + 4 per entry + 12
+    per coordinate + 8 k (output); the roofline reports the effective
+    fraction against HBM and the fraction against the L2 probe."""
+    assert bench._alg_bytes(3, 10, 11, 1, 4) == 12 + 24 + 40 + 132 + 32
+    assert bench._alg_bytes(0, 0, 0, 2, 1, extra_per_query=4) == 2 * 16 + 16
+    r = bench._roofline(1e9, 1.0, 1000, l2={"l2_read_gbs": 20000.0})
+    assert r["achieved"] == pytest.approx(1000.0)
+    assert r["frac"] == pytest.approx(1000.0 / r["peak"])
+    assert r["frac_l2"] == pytest.approx(0.05)
+    assert r["bound"] == "latency/divergence"
+    assert bench._roofline(1e9, 1.0, 1000)["frac_l2"] is None
+
+
+def test_oracle_pool_rate_on_a_tiny_sample():
+    """The multi-process oracle timing runs the oracle as it stands on a
+    spawn pool and counts the queries it answered."""
+    import workloads as W
+    P, _ = W.sphere(500, 3)
+    Q = W.box_queries(200, 4, [-1.5] * 3, [1.5] * 3)
+    rate, s, dt, cores = bench.oracle_rate(P, Q, 4, 0.2, cores=2)
+    assert cores == 2 and 4 <= s <= 196 and rate > 0 and dt > 0
