@@ -232,28 +232,36 @@ def _timed_ms(torch, stream, fn, steps: int, warmup: int, flush):
 
 
 def l2_probe(M, torch, dev, stream):
-    """L2 read bandwidth: a buffer of half the L2 size read 50 times per
-    launch with 16-byte loads through L2 (mknn_read_probe), best of 5."""
+    """L2 read bandwidth: buffers of a quarter and half of the L2 size
+    (two allocations each, since the placement across the L2 partitions
+    varies) read 50 times per launch with 16-byte loads through L2
+    (mknn_read_probe), best of 5 launches each; the best overall."""
     l2 = int(getattr(torch.cuda.get_device_properties(dev), "L2_cache_size", 0) or 0)
     if l2 <= 0:
         return None
-    nbytes = (l2 // 2) // 16 * 16
-    buf = torch.ones(nbytes // 4, dtype=torch.int32, device=dev)
-    sink = torch.zeros(1, dtype=torch.int32, device=dev)
     s = stream.cuda_stream
     passes = 50
-    M.mknn_read_probe(buf, nbytes, 2, sink, s)          # bring the buffer into L2
-    best = 0.0
-    for _ in range(5):
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        M.mknn_read_probe(buf, nbytes, passes, sink, s)
-        b.record(stream)
-        torch.cuda.synchronize()
-        best = max(best, nbytes * passes / (a.elapsed_time(b) / 1e3) / 1e9)
-    return {"l2_read_gbs": best, "buffer_bytes": nbytes, "l2_bytes": l2, "passes": passes,
-            "how": "mknn_read_probe: 16-byte loads through L2 over a buffer of half the L2 "
-                   "size, 50 passes per launch, best of 5 launches (CUDA events)"}
+    sink = torch.zeros(1, dtype=torch.int32, device=dev)
+    best, per = 0.0, []
+    for frac in (4, 2, 4, 2):
+        nbytes = (l2 // frac) // 16 * 16
+        buf = torch.ones(nbytes // 4, dtype=torch.int32, device=dev)
+        M.mknn_read_probe(buf, nbytes, 2, sink, s)          # bring the buffer into L2
+        b = 0.0
+        for _ in range(5):
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            M.mknn_read_probe(buf, nbytes, passes, sink, s)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            b = max(b, nbytes * passes / (ev0.elapsed_time(ev1) / 1e3) / 1e9)
+        per.append({"buffer_bytes": nbytes, "gbs": b})
+        best = max(best, b)
+        del buf
+    return {"l2_read_gbs": best, "l2_bytes": l2, "passes": passes, "runs": per,
+            "how": "mknn_read_probe: 16-byte loads through L2 over buffers of 1/4 and 1/2 of "
+                   "the L2 size (two allocations each), 50 passes per launch, best of 5 "
+                   "launches each (CUDA events); the best overall"}
 
 
 def _alg_bytes(rows, entries, coords, nq, k, extra_per_query=0):
@@ -531,7 +539,8 @@ def serving_section(args, M, torch, built=None):
     every run (arrival times scaled). Per load: requests per launch,
     p50/p99 latency, and the GPU time of each launch phase per request."""
     import workloads as W
-    wls, clouds, build_s = built if built is not None else (W.serve_clouds(), None, None)
+    wls, clouds, build_s = (built if built is not None
+                            else (W.serve_clouds(scale=args.scale), None, None))
     if clouds is None:
         clouds, build_s = _build_many(wls, "serve")
     for c in clouds:
@@ -596,18 +605,23 @@ def serving_section(args, M, torch, built=None):
     }
 
 
-# (lanes, slots per lane) of the persistent kernels, as the library's plans pick them
-_PLAN_VARIANTS = [(4, 1), (4, 2), (4, 4), (8, 1), (8, 2), (8, 4), (8, 8), (16, 1), (16, 2),
-                  (16, 4), (32, 1), (32, 2), (1, 64), (16, 8), (32, 4), (1, 128)]
+# (lanes, slots per lane, list placement) of the persistent kernels, as the
+# library's plans pick them (placement 2: shared memory, 1: registers)
+_PLAN_VARIANTS = [(4, 1, 1), (4, 2, 1), (4, 4, 1), (8, 1, 1), (8, 2, 1), (8, 4, 1), (8, 8, 1),
+                  (16, 1, 1), (16, 2, 1), (16, 4, 1), (32, 1, 1), (32, 2, 1), (1, 64, 2),
+                  (16, 8, 1), (32, 4, 1), (1, 128, 2), (32, 1, 2), (32, 2, 2), (32, 4, 2)]
 
 
-def _plan_launches(lanes, reqs) -> int:
+def _plan_launches(lanes, reqs, placement=None) -> int:
     """Kernels one plan replay launches: the locality sort's five per request
     of at least 4096 queries, and one persistent kernel per variant present
     (the fewest slots per lane that hold the request's k)."""
     variants = set()
-    for g, r in zip(lanes.tolist(), reqs):
-        fits = [v for v in _PLAN_VARIANTS if v[0] == g and v[0] * v[1] >= r["k"]]
+    placement = placement if placement is not None else [2 if g in (1, 32) else 1 for g in lanes]
+    for g, p, r in zip(lanes.tolist() if hasattr(lanes, "tolist") else lanes,
+                       placement.tolist() if hasattr(placement, "tolist") else placement, reqs):
+        lst = 2 if g == 1 else (p if g == 32 else 1)
+        fits = [v for v in _PLAN_VARIANTS if v[0] == g and v[2] == lst and v[0] * v[1] >= r["k"]]
         variants.add(min(fits, key=lambda v: v[1]))
     return len(variants) + 5 * sum(1 for r in reqs if r["nq"] >= 4096)
 
@@ -620,7 +634,8 @@ def batch_section(args, M, torch, built=None):
     latency: a request of the plan completes with the plan; a plain request
     completes with its own launch (CUDA events after each)."""
     import workloads as W
-    wls, clouds, build_s = built if built is not None else (W.batch_clouds(), None, None)
+    wls, clouds, build_s = (built if built is not None
+                            else (W.batch_clouds(scale=args.scale), None, None))
     if clouds is None:
         clouds, build_s = _build_many(wls, "batch")
     dev = torch.device("cuda", torch.cuda.current_device())
@@ -638,6 +653,7 @@ def batch_section(args, M, torch, built=None):
     tune_s = time.perf_counter() - t0
     plan = M.mknn_batch_create(reqs)
     lanes, items, grid = M.mknn_batch_info(plan, len(reqs))
+    placement = M.mknn_batch_placement(plan, len(reqs))
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
     nq = int(sum(r["nq"] for r in reqs))
     # algorithmic bytes of one pass over every request (counting kernel, untimed)
@@ -687,9 +703,12 @@ def batch_section(args, M, torch, built=None):
         "roofline": _roofline(alg, t_b, nq, l2=args._l2, kernel="knn_batch_* (persistent)"),
         "config": {"items": items, "grid": grid, "l2": "flushed before every timed step",
                    "lanes_chosen": {str(l): int((lanes == l).sum()) for l in set(lanes.tolist())},
+                   "modes_chosen": {f"{l} lanes, {'shared memory' if p == 2 else 'registers'}":
+                                    int(((lanes == l) & (placement == p)).sum())
+                                    for l, p in set(zip(lanes.tolist(), placement.tolist()))},
                    "tune_seconds": tune_s,
                    "build_seconds_max": build_s if build_s is not None else "cached"},
-        "gpu_launches_per_step": _plan_launches(lanes, reqs),
+        "gpu_launches_per_step": _plan_launches(lanes, reqs, placement),
         "clocks": clk,
     }
 
@@ -708,7 +727,10 @@ def prefix_section(args, M, torch, built=None):
     """Prefix workload: 4M-site bumpy sphere, 8M queries (half volume, half
     near-surface), per-query m log-uniform in [1000, n], k = 10."""
     import workloads as W
-    wl, cloud, build_s = built if built is not None else (W.prefix_bumpy(), None, None)
+    wl, cloud, build_s = (built if built is not None
+                          else (W.prefix_bumpy(n=max(2000, int(4_000_000 * args.scale)),
+                                               nq=max(1000, int(8_000_000 * args.scale))),
+                                None, None))
     if cloud is None:
         cloud, build_s = _cloud_cache(wl.points, wl.order, f"bumpy{wl.n}")
     cloud.upload()

@@ -221,9 +221,12 @@ mknn_status mknn_knn(const mknn_cloud* cloud, const float* q, int64_t nq, int32_
 
 /* Tuning knobs of one query launch; zero-initialise for defaults. */
 typedef struct {
-  int32_t lanes;        /* lanes per query: 0 = default, or 1, 4, 8, 16, 32
-                           (4 and 8 hold k <= 64; one lane above 64
-                           needs placement 2 and no counters) */
+  int32_t lanes;        /* lanes per query: 0 = default (1, or 32 from
+                           k = 48 up, or more for small batches and
+                           clouds with very long successor lists), or
+                           1, 4, 8, 16, 32 (4 and 8 hold k <= 64; one
+                           lane above 64 needs placement 2 and no
+                           counters) */
   int32_t sort;         /* query locality sort: 0 = default (on from 4096
                            queries), 1 = on, -1 = off */
   int32_t blocks_per_sm;/* 0 = default: one block per 256 queries for the
@@ -238,9 +241,12 @@ typedef struct {
   size_t workspace_bytes;
   const int32_t* order; /* device int32[nq] processing order (e.g. from
                            mknn_query_order) or NULL; overrides sort */
-  int32_t placement;    /* candidate list of a one-lane query: 0 = default
-                           (2), 1 = registers, 2 = shared memory (sorted
-                           64-bit keys) */
+  int32_t placement;    /* where the candidate list lives, for 1 and 32
+                           lanes: 0 = default (2), 1 = registers (one
+                           lane: per thread; 32 lanes: spread over the
+                           warp), 2 = shared memory (one lane: a list per
+                           thread; 32 lanes: one list per warp, not with
+                           counters); 4, 8, 16 lanes use registers */
   int32_t reserved[3];
 } mknn_knn_opts;
 
@@ -354,7 +360,11 @@ typedef struct {
                              fewer for a plan too small to fill the GPU) */
   int32_t blocks_per_sm;  /* 0 = occupancy limit */
   int32_t graph;          /* 0 = capture a CUDA graph (default), -1 = plain launches */
-  int32_t reserved[7];
+  int32_t placement;      /* with lanes set: 0 = that width's default, 1 = registers,
+                             2 = shared memory (only 32 lanes have both: a list
+                             per warp in shared memory, or spread over the
+                             warp's registers); with lanes 0: tuned per request */
+  int32_t reserved[6];
 } mknn_batch_opts;
 
 typedef struct mknn_batch mknn_batch;
@@ -374,6 +384,9 @@ mknn_status mknn_batch_run(mknn_batch* plan, mknn_stream_t stream);
  * blocks of the plan's persistent launches (one launch per kernel variant
  * present, summed). */
 mknn_status mknn_batch_info(const mknn_batch* plan, int32_t* lanes, int64_t* items, int32_t* grid);
+/* Candidate-list placement chosen per request (int32[nreq]; 2 = shared
+ * memory, 1 = registers), beside the lanes mknn_batch_info reports. */
+mknn_status mknn_batch_placement(const mknn_batch* plan, int32_t* placement);
 mknn_status mknn_batch_free(mknn_batch* plan);
 /* One-shot: create (without a graph), run, synchronise the stream, free. */
 mknn_status mknn_knn_batch(const mknn_batch_req* reqs, int32_t nreq, const mknn_batch_opts* opts,
@@ -382,20 +395,24 @@ mknn_status mknn_knn_batch(const mknn_batch_req* reqs, int32_t nreq, const mknn_
 /* Autotuner: for every distinct (k, floor(log2 n), floor(log2(1 + longest
  * successor list))) among the requests - the last separates clouds with
  * hub rows (nearly coplanar sites), whose queries cost far more -
- * times each kernel variant - one query per thread with a shared-memory
- * candidate list (lanes 1), or a group of 4, 8, 16 or 32 lanes with the
- * list in registers - on max(sample, 2 x SMs x 2048) queries of that
- * request (tiled when it has fewer; plain launches, best of 2 after a
- * warm-up) and records the fastest in the process-wide tuning table. Plans,
- * plain launches and the server take the table's entry, widened to more
- * lanes when a launch is too small to fill the GPU one query per thread.
- * If the environment variable MKNN_TUNE_LOG names a file, one line per
- * timed candidate (k, n, hub bucket, sample, lanes, ms) is appended to it.
- * Synchronises the stream. Errors: EINVAL, ENOMEM, ECUDA. */
+ * times each kernel variant and list placement: one query per thread with
+ * a shared-memory list (lanes 1), a group of 4, 8, 16 or 32 lanes with the
+ * list in registers, or one warp per query with the list in shared memory
+ * (lanes 32, placement 2). Each candidate runs as the persistent plan
+ * variant a plan would run (a one-request plan, no graph, best of 2 after a
+ * warm-up) on max(sample, 2 x SMs x 2048) queries of that request (tiled
+ * when it has fewer); the fastest (lanes, placement) goes into the
+ * process-wide tuning table. Plans, plain launches and the server take the
+ * table's entry, widened to more lanes when a launch is too small to fill
+ * the GPU one query per thread. If the environment variable MKNN_TUNE_LOG
+ * names a file, one line per timed candidate (k, n, hub bucket, sample,
+ * lanes, placement, ms) is appended to it. Synchronises the stream.
+ * Errors: EINVAL, ENOMEM, ECUDA. */
 mknn_status mknn_batch_tune(const mknn_batch_req* reqs, int32_t nreq, int64_t sample,
                             mknn_stream_t stream);
-/* Tuning table as text ("k log2n hub lanes" per line); load merges into
- * the table, clear empties it (the untuned defaults apply again). */
+/* Tuning table as text ("k log2n hub lanes placement" per line; a line
+ * without placement means that width's default); load merges into the
+ * table, clear empties it (the untuned defaults apply again). */
 mknn_status mknn_tune_save(const char* path);
 mknn_status mknn_tune_load(const char* path);
 mknn_status mknn_tune_clear(void);

@@ -38,26 +38,35 @@ namespace {
 
 constexpr int kThreads = 256;
 
-// Variants compiled into the persistent kernels: (G, S), list capacity G*S.
+// Variants compiled into the persistent kernels: (G, S, list), list
+// capacity G*S. list 2: shared memory (G = 1: a list per thread, any
+// k <= 64 or <= 128; G = 32: one list per warp); list 1: the group's
+// registers.
 struct VariantDesc {
-  int g, s;
+  int g, s, list;
 };
-// G = 1 is one query per thread with its candidate list in shared memory
-// (any k <= 64); the others keep a group's list in registers.
-constexpr VariantDesc kVariants[] = {{4, 1},  {4, 2},  {4, 4},  {8, 1},  {8, 2},
-                                     {8, 4},  {8, 8},  {16, 1}, {16, 2}, {16, 4},
-                                     {32, 1}, {32, 2}, {1, 64}, {16, 8}, {32, 4},
-                                     {1, 128}};
+constexpr VariantDesc kVariants[] = {{4, 1, 1},  {4, 2, 1},  {4, 4, 1},  {8, 1, 1},
+                                     {8, 2, 1},  {8, 4, 1},  {8, 8, 1},  {16, 1, 1},
+                                     {16, 2, 1}, {16, 4, 1}, {32, 1, 1}, {32, 2, 1},
+                                     {1, 64, 2}, {16, 8, 1}, {32, 4, 1}, {1, 128, 2},
+                                     {32, 1, 2}, {32, 2, 2}, {32, 4, 2}};
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 static_assert(kVariants[kSmemVariant].g == 1 && kVariants[kSmemVariant128].g == 1,
               "one-lane variant indices");
+static_assert(kVariants[kWarpVariant32].g == 32 && kVariants[kWarpVariant32].list == 2 &&
+                  kVariants[kWarpVariant32 + 2].s == 4,
+              "warp variant indices");
 
 }  // namespace
 
-int variant_index(int g, int k) {
+int variant_index(int g, int k, int placement) {
+  // one lane always keeps its list in shared memory in a plan; 4, 8 and 16
+  // lanes always in registers
+  const int list = g == 1 ? 2 : (g == 32 ? (placement == 2 ? 2 : 1) : 1);
   int best = -1;
   for (int i = 0; i < kNumVariants; ++i)
-    if (kVariants[i].g == g && kVariants[i].g * kVariants[i].s >= k && k >= 1) {
+    if (kVariants[i].g == g && kVariants[i].list == list && kVariants[i].g * kVariants[i].s >= k &&
+        k >= 1) {
       if (best < 0 || kVariants[i].s < kVariants[best].s) best = i;
     }
   return best;
@@ -161,6 +170,46 @@ __global__ void __launch_bounds__(THREADS, THREADS == 256 ? 5 : 1) knn_batch_sme
   }
 }
 
+// One warp per query, its candidate list in shared memory (KC keys per
+// warp, static): the warp takes an item and answers its queries one after
+// another.
+template <int KC>
+__global__ void __launch_bounds__(kThreads) knn_batch_warp_kernel(const ReqDev* __restrict__ reqs,
+                                                                  const Item* __restrict__ items,
+                                                                  int nitems,
+                                                                  int* __restrict__ next,
+                                                                  int kcap) {
+  (void)kcap;
+  __shared__ uint64_t lists[kThreads / 32][KC];
+  const int warp = (int)(threadIdx.x >> 5);
+  const uint32_t lane = threadIdx.x & 31u;
+  for (;;) {
+    int it = 0;
+    if (lane == 0) it = atomicAdd(next, 1);
+    it = __shfl_sync(0xffffffffu, it, 0);
+    if (it >= nitems) return;
+    const Item w = items[it];
+    const ReqDev& R = reqs[w.req];
+    const CloudDev C{R.pts, R.rows, R.succ, R.n, R.ent};
+    for (int i = w.begin; i < w.end; ++i) {
+      const int64_t qi = R.perm ? (int64_t)__ldg(R.perm + i) : (int64_t)i;
+      const float* qp = R.q + qi * R.q_stride;
+      const float qx = __ldg(qp), qy = __ldg(qp + 1), qz = __ldg(qp + 2);
+      const int m = R.m ? __ldg(R.m + qi) : R.m_scalar;
+      if (m < 1 || m > C.n) {
+        for (int p = (int)lane; p < R.k; p += 32) {
+          R.out_idx[qi * R.k + p] = -1;
+          R.out_d2[qi * R.k + p] = __int_as_float(0x7f800000);
+        }
+        if (lane == 0) atomicOr(R.err, 1);
+        continue;
+      }
+      knn_query_warp<KC>(C, qx, qy, qz, R.k, m, lists[warp], R.out_idx, R.out_d2, (int32_t)qi);
+    }
+    __syncwarp();
+  }
+}
+
 size_t list_bytes(int threads, int kcap) { return (size_t)threads * (size_t)kcap * 8; }
 
 inline size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
@@ -176,7 +225,7 @@ struct TuneKey {
 };
 
 std::mutex g_tune_mu;
-std::map<TuneKey, int> g_tune;  // -> lanes
+std::map<TuneKey, Mode> g_tune;  // -> lanes and list placement
 
 int nbucket_of(int64_t n) {
   int b = 0;
@@ -213,11 +262,13 @@ int auto_item_rounds(int64_t warp_rounds) {
   return (int)std::max<int64_t>(1, std::min<int64_t>(8, warp_rounds / target));
 }
 
-int choose_lanes(int k, int64_t n, int hub, int64_t nq) {
-  const int t = tuned_lanes(k, n, hub);
-  int lanes = std::max(t ? t : heuristic_lanes(k, hub), fill_lanes(nq, k));
-  while (lanes < 32 && variant_index(lanes, k) < 0) lanes <<= 1;  // e.g. 4 lanes hold k <= 16
-  return lanes;
+Mode choose_mode(int k, int64_t n, int hub, int64_t nq) {
+  const Mode t = tuned_mode(k, n, hub);
+  const int base = t.lanes ? t.lanes : heuristic_lanes(k, hub);
+  int lanes = std::max(base, fill_lanes(nq, k));
+  while (lanes < 32 && variant_index(lanes, k, 1) < 0) lanes <<= 1;  // e.g. 4 lanes hold k <= 16
+  const int placement = (t.lanes && lanes == t.lanes) ? t.placement : default_placement(k, lanes);
+  return Mode{lanes, placement};
 }
 
 namespace {
@@ -267,6 +318,9 @@ const void* variant_kernel(int variant, int threads) {
     case 11: return (const void*)knn_batch_group_kernel<32, 2>;
     case 13: return (const void*)knn_batch_group_kernel<16, 8>;
     case 14: return (const void*)knn_batch_group_kernel<32, 4>;
+    case kWarpVariant32: return (const void*)knn_batch_warp_kernel<32>;
+    case kWarpVariant32 + 1: return (const void*)knn_batch_warp_kernel<64>;
+    case kWarpVariant32 + 2: return (const void*)knn_batch_warp_kernel<128>;
     case kSmemVariant:
       return threads == 256 ? (const void*)knn_batch_smem_kernel<256, 1>
                             : (const void*)knn_batch_smem_kernel<128, 2>;
@@ -353,15 +407,15 @@ cudaError_t launch_segments(const ReqDev* d_reqs, const Item* d_items, int* d_ne
   return cudaStreamWaitEvent(s, join, 0);
 }
 
-int tuned_lanes(int k, int64_t n, int hub) {
+Mode tuned_mode(int k, int64_t n, int hub) {
   std::lock_guard<std::mutex> lk(g_tune_mu);
   auto it = g_tune.find(TuneKey{k, nbucket_of(n), hub});
-  return it == g_tune.end() ? 0 : it->second;
+  return it == g_tune.end() ? Mode{0, 0} : it->second;
 }
 
-void set_tuned_lanes(int k, int64_t n, int hub, int lanes) {
+void set_tuned_mode(int k, int64_t n, int hub, Mode m) {
   std::lock_guard<std::mutex> lk(g_tune_mu);
-  g_tune[TuneKey{k, nbucket_of(n), hub}] = lanes;
+  g_tune[TuneKey{k, nbucket_of(n), hub}] = m;
 }
 
 }  // namespace mknn
@@ -374,6 +428,7 @@ struct mknn_batch {
   std::vector<mknn_batch_req> reqs;
   std::vector<uint64_t> gens;    // each request's cloud generation when the plan was made
   std::vector<int> lanes;        // chosen lanes per request
+  std::vector<int> placement;    // and list placement (2 shared memory, 1 registers)
   ReqDev* d_reqs = nullptr;
   // work items grouped by kernel variant, one queue counter per segment
   Item* d_items = nullptr;
@@ -452,6 +507,7 @@ mknn_status mknn_batch_create(const mknn_batch_req* reqs, int32_t nreq,
   b->gens.resize(nreq);
   for (int r = 0; r < nreq; ++r) b->gens[r] = reqs[r].cloud ? reqs[r].cloud->generation.load() : 0;
   b->lanes.resize(nreq);
+  b->placement.resize(nreq);
   b->cell_off.assign(nreq, 0);
   b->perm_off.assign(nreq, 0);
   std::vector<ReqDev> rd(nreq);
@@ -474,10 +530,14 @@ mknn_status mknn_batch_create(const mknn_batch_req* reqs, int32_t nreq,
     }
     if (R.nq > 0 && (!R.q || !R.out_idx || !R.out_d2))
       return bfail(MKNN_EINVAL, "request " + std::to_string(r) + ": NULL device pointer");
-    const int lanes = o.lanes ? o.lanes : choose_lanes(R.k, R.cloud->n, R.cloud->hub_bucket(), plan_nq);
-    if (variant_index(lanes, R.k) < 0)
+    const Mode chosen = choose_mode(R.k, R.cloud->n, R.cloud->hub_bucket(), plan_nq);
+    const int lanes = o.lanes ? o.lanes : chosen.lanes;
+    const int placement = o.placement ? o.placement
+                                      : (o.lanes ? default_placement(R.k, lanes) : chosen.placement);
+    if (variant_index(lanes, R.k, placement) < 0)
       return bfail(MKNN_EINVAL, "request " + std::to_string(r) + ": lanes/k combination");
     b->lanes[r] = lanes;
+    b->placement[r] = placement;
     const CloudDevHost cd = R.cloud->dev();
     rd[r] = ReqDev{(const float4*)cd.pts, cd.rows,   cd.succ, cd.n,  R.q_stride,
                    R.q,                   R.m,       nullptr, R.out_idx,
@@ -507,7 +567,7 @@ mknn_status mknn_batch_create(const mknn_batch_req* reqs, int32_t nreq,
   std::vector<int> req_k(nreq);
   for (int r = 0; r < nreq; ++r) req_k[r] = reqs[r].k;
   for (int r : orderq) {
-    const int v = variant_index(b->lanes[r], reqs[r].k);
+    const int v = variant_index(b->lanes[r], reqs[r].k, b->placement[r]);
     const int per = item_queries(b->lanes[r], rounds);
     for (int64_t s0 = 0; s0 < reqs[r].nq; s0 += per)
       items.push_back(Item{r, (int32_t)s0, (int32_t)std::min<int64_t>(reqs[r].nq, s0 + per), v});
@@ -602,6 +662,12 @@ mknn_status mknn_batch_info(const mknn_batch* b, int32_t* lanes_out, int64_t* it
   return MKNN_OK;
 }
 
+mknn_status mknn_batch_placement(const mknn_batch* b, int32_t* placement_out) {
+  if (!b || (!placement_out && b->nreq > 0)) return bfail(MKNN_EINVAL, "NULL argument");
+  for (int r = 0; r < b->nreq; ++r) placement_out[r] = b->placement[r];
+  return MKNN_OK;
+}
+
 mknn_status mknn_batch_free(mknn_batch* b) {
   free_plan(b);
   return MKNN_OK;
@@ -623,8 +689,9 @@ mknn_status mknn_knn_batch(const mknn_batch_req* reqs, int32_t nreq, const mknn_
   return MKNN_OK;
 }
 
-// Times each candidate lane width on a sample of every distinct (k, size
-// bucket, hub bucket) among the requests and records the fastest in the tuning table.
+// Times each candidate (lanes, placement) on a sample of every distinct (k,
+// size bucket, hub bucket) among the requests, as the persistent plan
+// variant a plan would run, and records the fastest in the tuning table.
 mknn_status mknn_batch_tune(const mknn_batch_req* reqs, int32_t nreq, int64_t sample,
                             mknn_stream_t stream) {
   if (nreq < 0 || (nreq > 0 && !reqs)) return bfail(MKNN_EINVAL, "bad request array");
@@ -644,6 +711,7 @@ mknn_status mknn_batch_tune(const mknn_batch_req* reqs, int32_t nreq, int64_t sa
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   mknn_status st = MKNN_OK;
+  static const Mode kCandidates[] = {{1, 2}, {4, 1}, {8, 1}, {16, 1}, {32, 1}, {32, 2}};
   for (int r = 0; r < nreq && st == MKNN_OK; ++r) {
     const mknn_batch_req& R = reqs[r];
     if (!R.cloud || R.nq <= 0) continue;
@@ -678,17 +746,28 @@ mknn_status mknn_batch_tune(const mknn_batch_req* reqs, int32_t nreq, int64_t sa
                       cudaMemcpyDeviceToDevice, s);
       if (R.m) cudaMemcpyAsync(d_m + off, R.m, (size_t)len * 4, cudaMemcpyDeviceToDevice, s);
     }
-    int best = 0;
+    // the sample as one request of a one-request plan
+    mknn_batch_req T = R;
+    T.q = d_q;
+    T.nq = ns;
+    T.m = R.m ? d_m : nullptr;
+    T.out_idx = d_idx;
+    T.out_d2 = d_d2;
+    Mode best{0, 0};
     float best_ms = 1e30f;
-    for (int lanes : {1, 4, 8, 16, 32}) {
-      if (variant_index(lanes, R.k) < 0) continue;
-      mknn_knn_opts ko{};
-      ko.lanes = lanes;
+    for (const Mode& cand : kCandidates) {
+      if (variant_index(cand.lanes, R.k, cand.placement) < 0) continue;
+      mknn_batch_opts bo{};
+      bo.lanes = cand.lanes;
+      bo.placement = cand.placement;
+      bo.graph = -1;
+      mknn_batch* plan = nullptr;
+      st = mknn_batch_create(&T, 1, &bo, &plan);
+      if (st != MKNN_OK) break;
       float ms_min = 1e30f;
-      for (int rep = 0; rep < 3; ++rep) {
+      for (int rep = 0; rep < 3 && st == MKNN_OK; ++rep) {
         cudaEventRecord(e0, s);
-        st = mknn_knn_ex(R.cloud, d_q, ns, R.q_stride, R.k, R.m ? d_m : nullptr, R.m_scalar,
-                         d_idx, d_d2, &ko, stream);
+        st = mknn_batch_run(plan, stream);
         cudaEventRecord(e1, s);
         if (st != MKNN_OK) break;
         cudaEventSynchronize(e1);
@@ -696,20 +775,22 @@ mknn_status mknn_batch_tune(const mknn_batch_req* reqs, int32_t nreq, int64_t sa
         cudaEventElapsedTime(&ms, e0, e1);
         if (rep > 0) ms_min = std::min(ms_min, ms);
       }
+      free_plan(plan);
       if (st != MKNN_OK) break;
       if (const char* logp = std::getenv("MKNN_TUNE_LOG")) {
         if (FILE* lf = std::fopen(logp, "a")) {
-          std::fprintf(lf, "k=%d n=%lld hub=%d sample=%lld lanes=%d ms=%.4f\n", R.k,
-                       (long long)R.cloud->n, key.hub, (long long)ns, lanes, ms_min);
+          std::fprintf(lf, "k=%d n=%lld hub=%d sample=%lld lanes=%d placement=%d ms=%.4f\n",
+                       R.k, (long long)R.cloud->n, key.hub, (long long)ns, cand.lanes,
+                       cand.placement, ms_min);
           std::fclose(lf);
         }
       }
       if (ms_min < best_ms) {
         best_ms = ms_min;
-        best = lanes;
+        best = cand;
       }
     }
-    if (st == MKNN_OK && best) set_tuned_lanes(R.k, R.cloud->n, key.hub, best);
+    if (st == MKNN_OK && best.lanes) set_tuned_mode(R.k, R.cloud->n, key.hub, best);
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -725,9 +806,10 @@ mknn_status mknn_tune_save(const char* path) {
   FILE* f = std::fopen(path, "w");
   if (!f) return bfail(MKNN_EIO, std::string("cannot open ") + path);
   std::lock_guard<std::mutex> lk(g_tune_mu);
-  std::fprintf(f, "# k log2(n) log2(1+longest list) lanes\n");
+  std::fprintf(f, "# k log2(n) log2(1+longest list) lanes placement\n");
   for (auto& kv : g_tune)
-    std::fprintf(f, "%d %d %d %d\n", kv.first.k, kv.first.nbucket, kv.first.hub, kv.second);
+    std::fprintf(f, "%d %d %d %d %d\n", kv.first.k, kv.first.nbucket, kv.first.hub,
+                 kv.second.lanes, kv.second.placement);
   return std::fclose(f) == 0 ? MKNN_OK : bfail(MKNN_EIO, "write failed");
 }
 
@@ -742,13 +824,14 @@ mknn_status mknn_tune_load(const char* path) {
   FILE* f = std::fopen(path, "r");
   if (!f) return bfail(MKNN_EIO, std::string("cannot open ") + path);
   char line[256];
-  std::map<TuneKey, int> t;
+  std::map<TuneKey, Mode> t;
   while (std::fgets(line, sizeof line, f)) {
     if (line[0] == '#') continue;
-    int k, nb, hub, lanes;
-    if (std::sscanf(line, "%d %d %d %d", &k, &nb, &hub, &lanes) == 4 &&
-        variant_index(lanes, k) >= 0)
-      t[TuneKey{k, nb, hub}] = lanes;
+    int k, nb, hub, lanes, placement = 0;
+    const int got = std::sscanf(line, "%d %d %d %d %d", &k, &nb, &hub, &lanes, &placement);
+    if (got < 4) continue;
+    if (got == 4 || placement == 0) placement = default_placement(k, lanes);
+    if (variant_index(lanes, k, placement) >= 0) t[TuneKey{k, nb, hub}] = Mode{lanes, placement};
   }
   std::fclose(f);
   std::lock_guard<std::mutex> lk(g_tune_mu);

@@ -36,8 +36,9 @@ struct Item {
   int32_t req, begin, end, variant;
 };
 
-// Variant index for lanes-per-query G and capacity k, or -1.
-int variant_index(int lanes, int k);
+// Variant index for lanes-per-query G, capacity k and list placement
+// (2 = shared memory, 1 = registers; only 32 lanes have both), or -1.
+int variant_index(int lanes, int k, int placement);
 // Queries per work item for the given lanes and rounds per item.
 inline int item_queries(int lanes, int rounds) { return (32 / lanes) * rounds; }
 // Rounds per item for a launch whose requests need `warp_rounds` warp
@@ -50,6 +51,15 @@ int auto_item_rounds(int64_t warp_rounds);
 constexpr int kSmemVariant = 12;
 constexpr int kSmemVariant128 = 15;
 inline bool is_smem_variant(int v) { return v == kSmemVariant || v == kSmemVariant128; }
+// Variant indices of the one-warp-per-query kernels with the list in shared
+// memory: kWarpVariant32 + 0, 1, 2 for k <= 32, 64, 128.
+constexpr int kWarpVariant32 = 16;
+
+// Lanes per query and where the candidate list lives (2 = shared memory,
+// 1 = registers).
+struct Mode {
+  int lanes = 0, placement = 0;
+};
 
 // Shape of one persistent launch: one kernel variant over a queue of items.
 struct BatchLaunch {
@@ -85,15 +95,15 @@ cudaError_t launch_segments(const ReqDev* d_reqs, const Item* d_items, int* d_ne
                             const std::vector<Segment>& segs, cudaStream_t s, cudaStream_t aux,
                             cudaEvent_t fork, cudaEvent_t join);
 
-// Lanes per query recorded by the tuner for (k, floor(log2 n)), 0 if none.
-// The tuning table is keyed by k, floor(log2 n) and the cloud's hub bucket
+// Mode recorded by the tuner for (k, n, hub), lanes 0 if none. The tuning
+// table is keyed by k, floor(log2 n) and the cloud's hub bucket
 // (floor(log2(1 + longest successor list))).
-int tuned_lanes(int k, int64_t n, int hub);
-void set_tuned_lanes(int k, int64_t n, int hub, int lanes);
-// Lanes per query for a launch of nq queries: the tuned (or default) value
-// for (k, n, hub), widened for batches too small to fill the GPU one query
-// per thread.
-int choose_lanes(int k, int64_t n, int hub, int64_t nq);
+Mode tuned_mode(int k, int64_t n, int hub);
+void set_tuned_mode(int k, int64_t n, int hub, Mode m);
+// Mode for a launch of nq queries: the tuned (or default) lanes for
+// (k, n, hub), widened for batches too small to fill the GPU one query per
+// thread, and the tuned placement (or the default for those lanes).
+Mode choose_mode(int k, int64_t n, int hub, int64_t nq);
 // The smallest lane width that fills the GPU with nq queries of this k.
 int fill_lanes(int64_t nq, int k);
 

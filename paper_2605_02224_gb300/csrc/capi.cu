@@ -516,7 +516,8 @@ mknn_status mknn_knn_ex(const mknn_cloud* c, const float* q, int64_t nq, int32_t
   }
   if (nq == 0) return MKNN_OK;
   if (!q || !out_idx || !out_d2) return fail(MKNN_EINVAL, "NULL device pointer");
-  int lanes = (opts && opts->lanes) ? opts->lanes : choose_lanes(k, c->n, c->hub_bucket(), nq);
+  const Mode chosen = choose_mode(k, c->n, c->hub_bucket(), nq);
+  int lanes = (opts && opts->lanes) ? opts->lanes : chosen.lanes;
   if (lanes != 1 && lanes != 4 && lanes != 8 && lanes != 16 && lanes != 32)
     return fail(MKNN_EINVAL, "lanes must be 1, 4, 8, 16 or 32");
   if (k > plain_max_k(lanes))
@@ -555,7 +556,9 @@ mknn_status mknn_knn_ex(const mknn_cloud* c, const float* q, int64_t nq, int32_t
   L.err = c->d_err;
   L.lanes = lanes;
   L.blocks_per_sm = opts ? opts->blocks_per_sm : 0;
-  L.placement = (opts && opts->placement) ? opts->placement : default_placement(k);
+  L.placement = (opts && opts->placement)
+                    ? opts->placement
+                    : ((opts && opts->lanes) ? default_placement(k, lanes) : chosen.placement);
   if (L.placement != 1 && L.placement != 2)
     return fail(MKNN_EINVAL, "placement must be 0, 1 (registers) or 2 (shared memory)");
   cudaError_t e = launch_knn_plain(c->dev(), L, s);

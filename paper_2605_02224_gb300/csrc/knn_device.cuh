@@ -816,6 +816,187 @@ __device__ __forceinline__ void knn_query_smem_any(const CloudDev& C, float qx, 
   }
 }
 
+// ---------------------------------------------------------------------------
+// One warp per query with the candidate list N in shared memory (for large
+// k, where one list per thread would leave a few warps per SM). The list is
+// the warp's KC keys (KC = 32, 64 or 128 >= k), ascending, pads past cnt;
+// lane l owns positions l + 32 j. A row is read 32 entries at a time
+// (one coalesced 512-byte load of inlined entries); in the descent the
+// first strictly closer entry in list order is the lowest lane that votes
+// closer. In the expansion each lane whose entry falls below the k-th key
+// searches the list for it (a binary search in shared memory, all such
+// lanes at once): most of them are already in N (at k = 100, 781 of 948
+// per query on the 1M torus), and only the new ones are inserted, one at a
+// time by the whole warp: every lane compares its J keys, the votes give
+// the position, and the tail moves up by one slot. Expanded flags are kept
+// by position, the same in every lane.
+template <int KC>
+struct WarpList {
+  static constexpr int J = KC / 32;
+  uint64_t* L;          // the warp's KC keys in shared memory
+  int cnt;
+  uint32_t done[J];     // bit b of word j: position 32 j + b expanded
+  uint64_t worst;       // key of position k-1 (a pad while cnt < k)
+
+  __device__ __forceinline__ void init(uint64_t* list, int lane) {
+    L = list;
+    cnt = 0;
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+      done[j] = 0;
+      L[lane + 32 * j] = kPadKey;
+    }
+    worst = kPadKey;
+    __syncwarp();
+  }
+  // bits at position pos and above move up by one (an insertion at pos)
+  __device__ __forceinline__ void open_flag(int pos) {
+    const int wi = pos >> 5, bi = pos & 31;
+#pragma unroll
+    for (int j = J - 1; j >= 0; --j) {
+      if (j > wi) {
+        done[j] = (done[j] << 1) | (j > 0 ? (done[j > 0 ? j - 1 : 0] >> 31) : 0u);
+      } else if (j == wi) {
+        const uint32_t f = done[j];
+        const uint32_t low = bi ? (f & (~0u >> (32 - bi))) : 0u;
+        done[j] = low | ((f >> bi) << 1 << bi);
+      }
+    }
+  }
+  __device__ __forceinline__ void set_flag(int pos) {
+#pragma unroll
+    for (int j = 0; j < J; ++j)
+      if (j == (pos >> 5)) done[j] |= 1u << (pos & 31);
+  }
+  // first position below lim not yet expanded, or -1
+  __device__ __forceinline__ int first_clear(int lim) const {
+    int r = -1;
+#pragma unroll
+    for (int j = J - 1; j >= 0; --j) {
+      const int nb = max(0, min(32, lim - 32 * j));
+      const uint32_t c = ~done[j] & (nb == 32 ? ~0u : ((1u << nb) - 1u));
+      if (c) r = 32 * j + __ffs((int)c) - 1;
+    }
+    return r;
+  }
+  // is key c in the list? (called by any subset of lanes)
+  __device__ __forceinline__ bool contains(uint64_t c) const {
+    int pos = 0;
+#pragma unroll
+    for (int step = KC / 2; step >= 1; step >>= 1)
+      if (L[pos + step - 1] < c) pos += step;
+    return L[pos] == c;
+  }
+  // Inserts key c (the same in every lane; called by the whole warp) unless
+  // present; keeps k entries.
+  __device__ __forceinline__ void insert(uint64_t c, int k, int lane) {
+    uint64_t old[J], prev[J];
+    int less = 0;
+    bool eq = false;
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+      const int p = lane + 32 * j;
+      old[j] = L[p];
+      prev[j] = p ? L[p - 1] : 0ull;
+      less += __popc(__ballot_sync(0xffffffffu, old[j] < c));
+      eq |= old[j] == c;
+    }
+    if (__any_sync(0xffffffffu, eq) || less >= k) return;
+    const int pos = less;
+    __syncwarp();  // every lane has read its old and previous keys
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+      const int p = lane + 32 * j;
+      if (p < k) {
+        if (p > pos)
+          L[p] = prev[j];
+        else if (p == pos)
+          L[p] = c;
+      }
+    }
+    __syncwarp();
+    open_flag(pos);
+    if (cnt < k) cnt++;
+    if (cnt == k) worst = L[k - 1];
+  }
+};
+
+// One query by one warp (every lane calls it with the same query).
+template <int KC>
+__device__ __forceinline__ void knn_query_warp(const CloudDev& C, float qx, float qy, float qz,
+                                               int k, int m, uint64_t* list,
+                                               int32_t* __restrict__ out_idx,
+                                               float* __restrict__ out_d2, int32_t row) {
+  const int lane = (int)(threadIdx.x & 31u);
+  WarpList<KC> N;
+  N.init(list, lane);
+  float dcur = sqd32(qx, qy, qz, __ldg(C.pts));
+  N.insert(pack_key(dcur, 0u), k, lane);
+  int cur = 0;  // the descent's current site, -1 once it is over
+  int2 rr = __ldg(C.rows);
+  int base = rr.x, end = rr.y;
+  for (;;) {
+    const int e = base + lane;
+    const bool valid = e < end;
+    float4 ps = make_float4(0.f, 0.f, 0.f, __int_as_float(0x7fffffff));
+    if (valid) ps = __ldg(C.ent + e);
+    const int s = __float_as_int(ps.w);
+    const bool inr = valid && s < m;  // rows ascend: past the first s >= m nothing is
+    const float d = sqd32(qx, qy, qz, ps);
+    const uint64_t key = pack_key(d, (uint32_t)s);
+    const bool row_done = __any_sync(0xffffffffu, valid && !inr) || base + 32 >= end;
+    if (cur >= 0) {
+      const bool cl = inr && strictly_closer_at(C, qx, qy, qz, d, ps, dcur, cur);
+      const uint32_t b = __ballot_sync(0xffffffffu, cl);
+      if (b) {
+        const int w = __ffs((int)b) - 1;
+        cur = __shfl_sync(0xffffffffu, s, w);
+        dcur = __shfl_sync(0xffffffffu, d, w);
+        const uint64_t kw = __shfl_sync(0xffffffffu, key, w);
+        if (kw < N.worst) N.insert(kw, k, lane);
+        rr = __ldg(C.rows + cur);
+        base = rr.x;
+        end = rr.y;
+        continue;
+      }
+      if (row_done) cur = -1;
+    } else {
+      const bool fresh = inr && key < N.worst && !N.contains(key);
+      uint32_t b = __ballot_sync(0xffffffffu, fresh);
+      while (b) {
+        const int j = __ffs((int)b) - 1;
+        b &= b - 1;
+        const uint64_t c = __shfl_sync(0xffffffffu, key, j);
+        if (c < N.worst) N.insert(c, k, lane);
+      }
+    }
+    if (!row_done) {
+      base += 32;
+      continue;
+    }
+    const int pos = N.first_clear(min(N.cnt, k - 1));
+    if (pos < 0) break;
+    N.set_flag(pos);
+    const int site = (int)(uint32_t)N.L[pos];
+    rr = __ldg(C.rows + site);
+    base = rr.x;
+    end = rr.y;
+  }
+  int32_t* oi = out_idx + (int64_t)row * k;
+  float* od = out_d2 + (int64_t)row * k;
+#pragma unroll
+  for (int j = 0; j < KC / 32; ++j) {
+    const int p = lane + 32 * j;
+    if (p < k) {
+      const bool real = p < N.cnt;
+      const uint64_t key = N.L[p];
+      __stcs(oi + p, real ? (int32_t)(uint32_t)key : -1);
+      __stcs(od + p, real ? __uint_as_float((uint32_t)(key >> 32)) : __int_as_float(0x7f800000));
+    }
+  }
+  __syncwarp();
+}
+
 // Writes a padded row (-1, +inf) for a query that cannot be served.
 template <int G>
 __device__ __forceinline__ void pad_row(const Grp<G>& g, int k, int32_t* oi, float* od) {

@@ -40,7 +40,10 @@ struct PlainLaunch {
   int32_t* err;          // device error word
   int lanes;             // 1, 4, 8, 16, 32
   int blocks_per_sm;     // 0 = occupancy limit
-  int placement = 1;     // lanes == 1: 1 = registers per thread, 2 = shared-memory lists
+  // lanes == 1: 1 = registers per thread, 2 = shared-memory list per thread;
+  // lanes == 32: 1 = registers spread over the warp, 2 = shared-memory list
+  // per warp; ignored for 4, 8, 16 lanes (registers)
+  int placement = 1;
 };
 
 // Launches the plain (one cloud) query kernel. Returns a CUDA error code.
@@ -70,8 +73,12 @@ cudaError_t launch_query_sort_split(const CloudDevHost& c, const float* q, int32
                                     int64_t nq, void* hist, int32_t* cell, int32_t* perm,
                                     cudaStream_t stream);
 
+// From this k up, one warp per query (its list in shared memory) is the
+// default instead of one thread per query.
+constexpr int kWarpMinK = 48;
 int default_lanes(int k);
-int default_placement(int k);
+// 2 (shared memory) for 1 and 32 lanes, 1 (registers) for 4, 8, 16.
+int default_placement(int k, int lanes);
 // Largest k the plain kernels hold with this many lanes per query.
 int plain_max_k(int lanes);
 // The current device's ordinal (-1 if it cannot be read) and its SM count

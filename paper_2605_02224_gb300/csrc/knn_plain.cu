@@ -212,6 +212,64 @@ cudaError_t run_smem(const CloudDevHost& c, const PlainLaunch& L, cudaStream_t s
   return cudaGetLastError();
 }
 
+// One warp per query, the candidate list in shared memory (KC keys per
+// warp: 8 KB per 256-thread block at KC = 128). One block per 8 queries of
+// the processing order, started by the hardware wherever a block ends.
+template <int KC>
+__global__ void __launch_bounds__(kThreads) knn_plain_warp_kernel(
+    CloudDev C, const float* __restrict__ q, int q_stride, int64_t nq, int k,
+    const int32_t* __restrict__ mq, int m_scalar, const int32_t* __restrict__ perm,
+    int32_t* __restrict__ out_idx, float* __restrict__ out_d2, int32_t* __restrict__ err) {
+  __shared__ uint64_t lists[kThreads / 32][KC];
+  const int warp = (int)(threadIdx.x >> 5), lane = (int)(threadIdx.x & 31u);
+  const int64_t nw = (int64_t)gridDim.x * (kThreads / 32);
+  for (int64_t i = (int64_t)blockIdx.x * (kThreads / 32) + warp; i < nq; i += nw) {
+    const int64_t qi = perm ? (int64_t)__ldg(perm + i) : i;
+    const float* qp = q + qi * q_stride;
+    const float qx = __ldg(qp), qy = __ldg(qp + 1), qz = __ldg(qp + 2);
+    const int m = mq ? __ldg(mq + qi) : m_scalar;
+    if (m < 1 || m > C.n) {
+      for (int p = lane; p < k; p += 32) {
+        out_idx[qi * k + p] = -1;
+        out_d2[qi * k + p] = __int_as_float(0x7f800000);
+      }
+      if (lane == 0) atomicOr(err, 1);
+      continue;
+    }
+    knn_query_warp<KC>(C, qx, qy, qz, k, m, lists[warp], out_idx, out_d2, (int32_t)qi);
+  }
+}
+
+template <int KC>
+cudaError_t run_warp(const CloudDevHost& c, const PlainLaunch& L, cudaStream_t stream) {
+  constexpr int kWarps = kThreads / 32;
+  int64_t blocks = (L.nq + kWarps - 1) / kWarps;
+  if (L.blocks_per_sm > 0) {
+    static PerDevice<int> occ_of;
+    int occ = 0;
+    const cudaError_t oe = occ_of.with(current_device(), cudaErrorInvalidDevice, [&](int& o) {
+      if (o < 1) {
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &o, knn_plain_warp_kernel<KC>, kThreads, 0);
+        if (e != cudaSuccess) {
+          o = 0;
+          return e;
+        }
+        if (o < 1) o = 1;
+      }
+      occ = o;
+      return cudaSuccess;
+    });
+    if (oe != cudaSuccess) return oe;
+    blocks = std::min<int64_t>(blocks, (int64_t)num_sms() * std::min(L.blocks_per_sm, occ));
+  }
+  if (blocks < 1) blocks = 1;
+  CloudDev C{(const float4*)c.pts, c.rows, c.succ, c.n, (const float4*)c.ent};
+  knn_plain_warp_kernel<KC><<<(unsigned)blocks, kThreads, 0, stream>>>(
+      C, L.q, L.q_stride, L.nq, L.k, L.m, L.m_scalar, L.perm, L.out_idx, L.out_d2, L.err);
+  return cudaGetLastError();
+}
+
 template <bool COUNT>
 cudaError_t pick_thread(const CloudDevHost& c, const PlainLaunch& L, cudaStream_t stream) {
   if (!COUNT && L.placement == 2) {
@@ -283,6 +341,11 @@ cudaError_t pick_s(const CloudDevHost& c, const PlainLaunch& L, cudaStream_t str
 
 template <bool COUNT>
 cudaError_t pick_g(const CloudDevHost& c, const PlainLaunch& L, cudaStream_t stream) {
+  if (!COUNT && L.lanes == 32 && L.placement == 2) {
+    if (L.k <= 32) return run_warp<32>(c, L, stream);
+    if (L.k <= 64) return run_warp<64>(c, L, stream);
+    return run_warp<128>(c, L, stream);
+  }
   switch (L.lanes) {
     case 1: return pick_thread<COUNT>(c, L, stream);
     case 4: return pick_s<4, COUNT>(c, L, stream);
@@ -369,20 +432,20 @@ cudaError_t launch_fill_entries(const void* pts, const int32_t* succ, int64_t E,
   return cudaGetLastError();
 }
 
-int default_lanes(int k) {
-  (void)k;
-  return 1;
-}
+// Measured on the 1M-site torus with 4M box queries (queries/s): one query
+// per thread with the list in shared memory against one warp per query with
+// the warp's list in shared memory: k = 32: 164M / 120M; k = 64: 51M / 54M;
+// k = 100: 21M / 26M; k = 128: 12M / 21M. Register lists over a group of
+// 32 (16) lanes: 61M (45M), 21M (7M), 8M (4M), 6M (3M).
+int default_lanes(int k) { return k >= kWarpMinK ? 32 : 1; }
 
-// One query per thread with the candidate list in shared memory is the
-// fastest variant measured at every k (1M-site torus, 4M box queries:
-// k=4 449M q/s, k=16 168M, k=32 60M, k=64 14M; registers: 368M, 125M,
-// 26M, 3M; best group of lanes: 264M, 111M, 44M, 13M).
 int plain_max_k(int lanes) { return (lanes == 4 || lanes == 8) ? 64 : 128; }
 
-int default_placement(int k) {
+// Shared-memory lists for one lane (per thread) and for 32 lanes (per
+// warp); the group kernels of 4, 8 and 16 lanes keep theirs in registers.
+int default_placement(int k, int lanes) {
   (void)k;
-  return 2;
+  return (lanes == 1 || lanes == 32) ? 2 : 1;
 }
 
 cudaError_t launch_knn_plain(const CloudDevHost& c, const PlainLaunch& L, cudaStream_t stream) {

@@ -119,7 +119,8 @@ extern "C" mknn_status mknn_knn_noalloc(const mknn_cloud* c, const float* q, int
     return MKNN_ECUDA;
   }
   // the kernel variant mknn_knn would take for this cloud and batch size
-  const int lanes = choose_lanes(k, c->n, c->hub_bucket(), nq);
+  const Mode mode = choose_mode(k, c->n, c->hub_bucket(), nq);
+  const int lanes = mode.lanes;
   if (k > plain_max_k(lanes)) {
     set_error("k above what the chosen lane width holds");
     return MKNN_EINVAL;
@@ -150,7 +151,7 @@ extern "C" mknn_status mknn_knn_noalloc(const mknn_cloud* c, const float* q, int
   L.counters = nullptr;
   L.err = c->d_err;
   L.lanes = lanes;
-  L.placement = default_placement(k);
+  L.placement = mode.placement;
   L.blocks_per_sm = 0;
   if ((e = launch_knn_plain(cd, L, s)) != cudaSuccess) {
     set_error(std::string("knn kernel launch: ") + cudaGetErrorString(e));

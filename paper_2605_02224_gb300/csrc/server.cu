@@ -258,12 +258,14 @@ void mknn_server::launch(Slot& sl, std::vector<uint64_t>& tickets, size_t off, s
     std::vector<int> req_k(nreq);
     int64_t pack_nq = 0;  // the pack runs as one launch per variant: its size sets the lanes
     for (int i = 0; i < nreq; ++i) pack_nq += recs[tickets[i] - 1].r.nq;
-    std::vector<int> lanes(nreq);
+    std::vector<int> lanes(nreq), placement(nreq);
     int64_t warp_rounds = 0;
     for (int i = 0; i < nreq; ++i) {
       const mknn_request& q = recs[tickets[i] - 1].r;
       const mknn_cloud* c = clouds[q.cloud];
-      lanes[i] = o.lanes ? o.lanes : choose_lanes(q.k, c->n, c->hub_bucket(), pack_nq);
+      const Mode chosen = choose_mode(q.k, c->n, c->hub_bucket(), pack_nq);
+      lanes[i] = o.lanes ? o.lanes : chosen.lanes;
+      placement[i] = o.lanes ? default_placement(q.k, lanes[i]) : chosen.placement;
       warp_rounds += (q.nq * lanes[i] + 31) / 32;
     }
     const int rounds = auto_item_rounds(warp_rounds);
@@ -285,7 +287,7 @@ void mknn_server::launch(Slot& sl, std::vector<uint64_t>& tickets, size_t off, s
                      sorted ? (const int32_t*)(dbase + R.perm_off) : nullptr,
                      (int32_t*)(dbase + R.idx_off), (float*)(dbase + R.d2_off), c->d_err, q.k,
                      q.m ? q.m : (int32_t)c->n, (const float4*)cd.ent};
-      const int v = variant_index(lanes[i], q.k);
+      const int v = variant_index(lanes[i], q.k, placement[i]);
       const int per = item_queries(lanes[i], rounds);
       req_k[i] = q.k;
       for (int64_t b0 = 0; b0 < q.nq; b0 += per)
@@ -428,7 +430,8 @@ mknn_status mknn_server_create(const mknn_server_opts* opts, mknn_server** out) 
   if (s->o.plain) s->o.slots = 1;
   if (s->o.mem_budget == 0) s->o.mem_budget = (size_t)3 << 30;
   if (s->o.max_batch_queries <= 0) s->o.max_batch_queries = (int64_t)1 << 17;
-  if (s->o.lanes && variant_index(s->o.lanes, 1) < 0) return sfail(MKNN_EINVAL, "bad lanes");
+  if (s->o.lanes && variant_index(s->o.lanes, 1, default_placement(1, s->o.lanes)) < 0)
+    return sfail(MKNN_EINVAL, "bad lanes");
   cudaGetDevice(&s->device);
   s->arena_bytes = al(s->o.mem_budget);
   cudaError_t e = cudaMalloc((void**)&s->d_arena, s->arena_bytes);

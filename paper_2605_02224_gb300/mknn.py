@@ -55,7 +55,8 @@ class mknn_batch_req(C.Structure):
 
 class mknn_batch_opts(C.Structure):
     _fields_ = [("lanes", C.c_int32), ("sort", C.c_int32), ("item_rounds", C.c_int32),
-                ("blocks_per_sm", C.c_int32), ("graph", C.c_int32), ("reserved", C.c_int32 * 7)]
+                ("blocks_per_sm", C.c_int32), ("graph", C.c_int32), ("placement", C.c_int32),
+                ("reserved", C.c_int32 * 6)]
 
 
 class mknn_server_opts(C.Structure):
@@ -135,6 +136,7 @@ def _declare(L):
         "mknn_batch_create": (i32, [vp, i32, vp, pp]),
         "mknn_batch_run": (i32, [vp, vp]),
         "mknn_batch_info": (i32, [vp, vp, vp, vp]),
+        "mknn_batch_placement": (i32, [vp, vp]),
         "mknn_batch_free": (i32, [vp]),
         "mknn_knn_batch": (i32, [vp, i32, vp, vp]),
         "mknn_batch_tune": (i32, [vp, i32, i64, vp]),
@@ -392,10 +394,11 @@ def batch_reqs(reqs):
     return arr
 
 
-def mknn_batch_create(reqs, lanes=0, sort=0, item_rounds=0, blocks_per_sm=0, graph=0) -> int:
+def mknn_batch_create(reqs, lanes=0, sort=0, item_rounds=0, blocks_per_sm=0, graph=0,
+                      placement=0) -> int:
     arr = batch_reqs(reqs)
     o = mknn_batch_opts(lanes=lanes, sort=sort, item_rounds=item_rounds,
-                        blocks_per_sm=blocks_per_sm, graph=graph)
+                        blocks_per_sm=blocks_per_sm, graph=graph, placement=placement)
     out = C.c_void_p()
     _check(lib().mknn_batch_create(arr, len(reqs), C.addressof(o), C.byref(out)))
     return out.value
@@ -410,6 +413,12 @@ def mknn_batch_info(plan: int, nreq: int):
     items, grid = C.c_int64(), C.c_int32()
     _check(lib().mknn_batch_info(plan, _ptr(lanes), C.byref(items), C.byref(grid)))
     return lanes[:nreq], items.value, grid.value
+
+
+def mknn_batch_placement(plan: int, nreq: int):
+    out = np.zeros(max(1, nreq), np.int32)
+    _check(lib().mknn_batch_placement(plan, _ptr(out)))
+    return out[:nreq]
 
 
 def mknn_batch_free(plan: int):

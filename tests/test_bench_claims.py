@@ -58,17 +58,28 @@ def test_plan_variant_table_matches_the_library():
     src = _read("batch.cu")
     init = src[src.index("constexpr VariantDesc kVariants[] = {"):]
     init = init[:init.index("};")]
-    table = [(int(a), int(b)) for a, b in re.findall(r"\{(\d+),\s*(\d+)\}", init)]
+    table = [(int(a), int(b), int(c))
+             for a, b, c in re.findall(r"\{(\d+),\s*(\d+),\s*(\d+)\}", init)]
     assert table == bench._PLAN_VARIANTS
     assert "reqs[r].nq < (o.sort > 0 ? 1 : 4096)" in src
+    h = open(os.path.join(CSRC, "batch.h")).read()
+    assert "constexpr int kWarpVariant32 = 16;" in h
+    assert table[16:19] == [(32, 1, 2), (32, 2, 2), (32, 4, 2)]
 
 
 def test_plan_launch_count():
     reqs = [dict(k=k, nq=nq) for k, nq in [(16, 20000), (32, 5000), (1, 100), (8, 3_000_000),
                                           (100, 9000)]]
     lanes = np.array([1, 32, 1, 1, 32])
-    # variants (1, 64) and (32, 1), (32, 4); four requests of >= 4096 queries
+    # variants (1, 64) and the warp kernels (32, 1), (32, 4) in shared memory;
+    # four requests of >= 4096 queries
     assert bench._plan_launches(lanes, reqs) == 3 + 5 * 4
+    # registers for the 32-lane requests: (32, 1) and (32, 4) register groups
+    assert bench._plan_launches(lanes, reqs, np.array([2, 1, 2, 2, 1])) == 3 + 5 * 4
+    # both placements at k = 32: two 32-lane variants
+    lanes2 = np.array([32, 32])
+    reqs2 = [dict(k=32, nq=10), dict(k=32, nq=10)]
+    assert bench._plan_launches(lanes2, reqs2, np.array([1, 2])) == 2
 
 
 def test_traffic_record_is_used_only_for_its_own_sources():

@@ -59,18 +59,21 @@ def _plain(torch, c, q, k, m, ms):
     return idx.cpu().numpy(), d2.cpu().numpy()
 
 
-@pytest.mark.parametrize("lanes", [0, 1, 4, 8, 16, 32])
-def test_batch_equals_plain_per_request(torch, clouds, lanes):
+@pytest.mark.parametrize("lanes,placement", [(0, 0), (1, 0), (4, 0), (8, 0), (16, 0), (32, 1),
+                                             (32, 2)])
+def test_batch_equals_plain_per_request(torch, clouds, lanes, placement):
     reqs, keep = _requests(torch, clouds, "array")
     kmax = {4: 16}.get(lanes, 64)     # variants compiled into the persistent kernel
     if any(r["k"] > kmax for r in reqs):
         bad = [dict(r) for r in reqs]
         with pytest.raises(M.MknnError) as ei:
-            M.mknn_knn_batch(bad, torch.cuda.current_stream().cuda_stream, lanes=lanes)
+            M.mknn_knn_batch(bad, torch.cuda.current_stream().cuda_stream, lanes=lanes,
+                             placement=placement)
         assert ei.value.status == 1
         reqs = [r for r in reqs if r["k"] <= kmax]
         keep = [kp for kp in keep if kp[0].k <= kmax]
-    M.mknn_knn_batch(reqs, torch.cuda.current_stream().cuda_stream, lanes=lanes)
+    M.mknn_knn_batch(reqs, torch.cuda.current_stream().cuda_stream, lanes=lanes,
+                     placement=placement)
     torch.cuda.synchronize()
     for wl, c, q, m, ms, idx, d2 in keep:
         pi, pd = _plain(torch, c, q, wl.k, m, ms)
@@ -110,6 +113,42 @@ def test_plan_with_many_variants_equals_plain(torch, clouds, tmp_path):
         M.mknn_tune_clear()
 
 
+def test_tuning_table_with_both_placements(torch, clouds, tmp_path):
+    """Table lines with a placement column: the same k on 32 lanes in
+    registers for some requests and one list per warp in shared memory for
+    others; the plan runs both kernels and every row equals a plain launch."""
+    reqs, keep = _requests(torch, clouds, "array")
+    modes = ((32, 1), (32, 2), (1, 2), (32, 2), (32, 1), (8, 1), (32, 2), (16, 1))
+    lines = []
+    for (wl, c, *_), (w, p) in zip(keep, modes):
+        longest = int(np.diff(c.table()[1]).max())
+        lines.append(f"{wl.k} {int(np.floor(np.log2(wl.n)))} "
+                     f"{int(np.floor(np.log2(1 + longest)))} {w} {p}\n")
+    path = tmp_path / "table.txt"
+    path.write_text("# k log2n hub lanes placement\n" + "".join(lines))
+    M.mknn_tune_clear()
+    M.mknn_tune_load(str(path))
+    try:
+        plan = M.mknn_batch_create(reqs)
+        lanes, _, _ = M.mknn_batch_info(plan, len(reqs))
+        pl = M.mknn_batch_placement(plan, len(reqs))
+        got = set(zip(lanes.tolist(), pl.tolist()))
+        assert (32, 1) in got and (32, 2) in got, got
+        M.mknn_batch_run(plan, torch.cuda.current_stream().cuda_stream)
+        torch.cuda.synchronize()
+        for wl, c, q, m, ms, idx, d2 in keep:
+            pi, pd = _plain(torch, c, q, wl.k, m, ms)
+            assert np.array_equal(idx.cpu().numpy(), pi), wl.name
+            assert np.array_equal(d2.cpu().numpy(), pd), wl.name
+        M.mknn_batch_free(plan)
+        saved = tmp_path / "saved.txt"
+        M.mknn_tune_save(str(saved))
+        rows = [l.split() for l in saved.read_text().splitlines() if not l.startswith("#")]
+        assert rows and all(len(r) == 5 for r in rows)
+    finally:
+        M.mknn_tune_clear()
+
+
 def test_large_k_requests_in_a_plan(torch, clouds):
     """Requests with k = 65, 100 and 128 (the one-lane kernel with 128-slot
     lists, or 16 and 32 lanes) mixed with the workload's own: the plan equals
@@ -122,8 +161,8 @@ def test_large_k_requests_in_a_plan(torch, clouds):
         reqs.append(dict(cloud=c.handle, q=q, nq=wl.nq, q_stride=3, k=k, m=None, m_scalar=0,
                          out_idx=idx, out_d2=d2))
         keep.append((wl, c, q, None, 0, idx, d2, k))
-    for forced in (0, 32, 16):
-        plan = M.mknn_batch_create(reqs, lanes=forced)
+    for forced, placement in ((0, 0), (32, 2), (32, 1), (16, 0)):
+        plan = M.mknn_batch_create(reqs, lanes=forced, placement=placement)
         lanes, _, _ = M.mknn_batch_info(plan, len(reqs))
         assert all(l in (1, 16, 32) for l in lanes[3:])
         M.mknn_batch_run(plan, torch.cuda.current_stream().cuda_stream)
@@ -193,12 +232,16 @@ def test_tuner_fills_table_and_plan_uses_it(torch, clouds, tmp_path):
     M.mknn_tune_load(path)
     plan = M.mknn_batch_create(reqs)
     lanes, _, _ = M.mknn_batch_info(plan, len(reqs))
-    table = {(int(a), int(b), int(h)): int(c) for a, b, h, c in (l.split() for l in lines)}
-    for (wl, c, *_), l in zip(keep, lanes):
+    placement = M.mknn_batch_placement(plan, len(reqs))
+    table = {(int(a), int(b), int(h)): (int(c), int(p))
+             for a, b, h, c, p in (l.split() for l in lines)}
+    for (wl, c, *_), l, p in zip(keep, lanes, placement):
         longest = int(np.diff(c.table()[1]).max())
         key = (wl.k, int(np.floor(np.log2(wl.n))), int(np.floor(np.log2(1 + longest))))
         assert key in table
-        assert table[key] == l or l > table[key]   # widened only to fill the GPU
+        assert table[key][0] == l or l > table[key][0]   # widened only to fill the GPU
+        if table[key][0] == l:
+            assert table[key][1] == p                     # the tuned placement is kept
     M.mknn_batch_run(plan, s)
     torch.cuda.synchronize()
     for wl, c, q, m, ms, idx, d2 in keep:

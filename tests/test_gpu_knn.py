@@ -15,11 +15,11 @@ from tests.gpu_util import built_cloud, run_knn
 pytestmark = pytest.mark.gpu
 
 LANES = (1, 4, 8, 16, 32)
-# lanes per query; one-lane candidate-list placement (1 = registers, 2 = shared
-# memory)
+# lanes per query; candidate-list placement for 1 and 32 lanes (1 = registers,
+# 2 = shared memory: a list per thread, or one per warp)
 VARIANTS = (dict(lanes=1, placement=1), dict(lanes=1, placement=2),
             dict(lanes=4, placement=1), dict(lanes=8, placement=1), dict(lanes=16, placement=1),
-            dict(lanes=32, placement=1))
+            dict(lanes=32, placement=1), dict(lanes=32, placement=2))
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -209,8 +209,8 @@ def test_large_k_with_prefix_bounds():
     m = np.clip(np.floor(np.exp(W.uniform(43, 1, nq) * np.log(20000))), 1, 20000).astype(np.int32)
     for k in (65, 100, 128):
         base = None
-        for lanes in (0, 1, 16, 32):
-            idx, d2 = run_knn(c, Q, k, m, lanes=lanes)
+        for lanes, placement in ((0, 0), (1, 2), (16, 1), (32, 1), (32, 2)):
+            idx, d2 = run_knn(c, Q, k, m, lanes=lanes, placement=placement)
             if base is None:
                 parity.check_row_properties(idx, d2, k, m.astype(np.int64), 20000)
                 parity.check_rows(Pr, Q, k, m, idx, d2, rows=range(0, nq, 3))
@@ -234,7 +234,8 @@ def test_degraded_manifold_and_uniform_volume(ratio):
     Pr = wl.ranked_points()
     idx, d2 = run_knn(c, wl.queries, 16)
     parity.check_rows(Pr, wl.queries, 16, 0, idx, d2)
-    for v in (dict(lanes=1, placement=1), dict(lanes=32, placement=1)):
+    for v in (dict(lanes=1, placement=1), dict(lanes=32, placement=1),
+              dict(lanes=32, placement=2)):
         i2, d22 = run_knn(c, wl.queries, 16, **v)
         assert np.array_equal(i2, idx) and np.array_equal(d22, d2)
     c.close()
