@@ -97,9 +97,16 @@ def _peaks():
         return 6800.0, "fallback"
 
 
+WARP_MIN_K = 48   # from this k the library's default is one warp per query
+
+
 def _query_kernel_name(lanes: int, k: int, placement: int) -> str:
     """The query kernel a plain launch with these options runs (its default:
-    one lane per query with the list in shared memory)."""
+    one lane per query with the list in shared memory, one warp per query
+    with the warp's list in shared memory from k = 48)."""
+    if (lanes == 0 and k >= WARP_MIN_K) or (lanes == 32 and placement in (0, 2)):
+        kc = 32 if k <= 32 else (64 if k <= 64 else 128)
+        return f"knn_plain_warp_kernel<{kc}>"
     if lanes in (0, 1) and placement in (0, 2):
         threads, words = (256, 1) if k <= 32 else ((128, 2) if k <= 64 else (64, 4))
         kind = 8 if k <= 8 else (16 if k <= 16 else 0)
@@ -668,8 +675,12 @@ def batch_section(args, M, torch, built=None):
                        r["out_d2"], s)
 
     def measure():
+        # an NVTX range around the plan's launches, so that a profiler can
+        # select them apart from the tuner's (ncu --nvtx --nvtx-include batch_plan/)
+        torch.cuda.nvtx.range_push("batch_plan")
         ms_batch = _timed_ms(torch, stream, lambda: M.mknn_batch_run(plan, s), args.steps,
                              args.warmup, flush)
+        torch.cuda.nvtx.range_pop()
         ref = [r["out_idx"].clone() for r in reqs]
         ms_plain = _timed_ms(torch, stream, plain, args.steps, args.warmup, flush)
         same = all(torch.equal(a, r["out_idx"]) for a, r in zip(ref, reqs))
@@ -774,17 +785,13 @@ def prefix_workload(args, M, torch):
     print(json.dumps(line), flush=True)
 
 
-def sites_workload(args, M, torch):
-    """Same-manifold queries: every site of the 1M-point torus queried
-    against the cloud (normal-estimation style, k = 16), and the same sites
-    probed across prefixes with k = 100 (m log-uniform in [1000, n], the
-    temporal setting of Sec. 5)."""
+def sites_section(args, M, torch, cloud, n):
+    """Same-manifold queries: every site of the cloud queried against it
+    (normal-estimation style, k = 16), and the same sites probed across
+    prefixes with k = 100 (m log-uniform in [1000, n], the temporal setting
+    of Sec. 5). Each run with its own clock samples and roofline."""
     import workloads as W
-    wl = W.large_torus(n=args.n, nq=1, k=16)
-    cloud, build_s = _cloud_cache(wl.points, wl.order, f"torus{wl.n}")
-    cloud.upload()
     dev = torch.device("cuda", torch.cuda.current_device())
-    n = wl.n
     sites = torch.from_numpy(W.permutation(n, 61).astype(np.int32)).to(dev)
     stream = torch.cuda.current_stream(dev)
     s = stream.cuda_stream
@@ -798,31 +805,33 @@ def sites_workload(args, M, torch):
             m = torch.from_numpy(mv.astype(np.int32)).to(dev)
         idx = torch.empty((n, k), dtype=torch.int32, device=dev)
         d2 = torch.empty((n, k), dtype=torch.float32, device=dev)
-        for _ in range(max(3, args.warmup)):
-            M.mknn_knn_sites(cloud.handle, sites, n, k, m, 0, idx, d2, s)
-        cnt = torch.zeros((n, 4), dtype=torch.int32, device=dev)
-        M.mknn_knn_sites(cloud.handle, sites, n, k, m, 0, idx, d2, s, counters=cnt,
-                         lanes=32 if k > 64 else 1)
-        torch.cuda.synchronize()
-        rows, entries, coords, trans = (int(x) for x in cnt.to(torch.int64).sum(dim=0).cpu().numpy())
-        alg = 4 * n + 12 * n + 8 * rows + 4 * entries + 12 * coords + 8 * k * n
-        ms = []
-        for i in range(args.steps):
-            flush.fill_(float(i))
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            M.mknn_knn_sites(cloud.handle, sites, n, k, m, 0, idx, d2, s)
-            b.record(stream)
-            torch.cuda.synchronize()
-            ms.append(a.elapsed_time(b))
+        rows, entries, coords, trans = _counts(M, torch, cloud, None, n, k, m, s, sites=sites)
+        alg = _alg_bytes(rows, entries, coords, n, k, extra_per_query=4 + (4 if m is not None
+                                                                         else 0))
+        ms, clk = _clocked(dev.index, lambda: _timed_ms(
+            torch, stream, lambda: M.mknn_knn_sites(cloud.handle, sites, n, k, m, 0, idx, d2, s),
+            args.steps, args.warmup, flush))
         t = float(np.mean(ms))
-        peak, kind = _peaks()
         out[f"k{k}"] = {"workload": f"torus n={n}, {n} site queries ({mode}), k={k}",
-                        "value": n / (t / 1e3), "ms_per_step": t,
-                        "alg_bytes_per_query": alg / n,
-                        "roofline_frac": alg / (t / 1e3) / 1e9 / peak,
-                        "counts_per_query": {"rows": rows / n, "entries": entries / n,
-                                             "transitions": trans / n}}
+                        "value": n / (t / 1e3), "unit": UNIT, "ms_per_step": t,
+                        "roofline": _roofline(alg, t, n, l2=args._l2,
+                                              kernel=_query_kernel_name(0, k, 0),
+                                              counts={"rows": rows / n, "entries": entries / n,
+                                                      "coords": coords / n,
+                                                      "transitions": trans / n}),
+                        "clocks": clk}
+        del idx, d2
+    return out
+
+
+def sites_workload(args, M, torch):
+    import workloads as W
+    wl = W.large_torus(n=args.n, nq=1, k=16)
+    cloud, build_s = _cloud_cache(wl.points, wl.order, f"torus{wl.n}")
+    cloud.upload()
+    args._l2 = l2_probe(M, torch, torch.device("cuda", torch.cuda.current_device()),
+                        torch.cuda.current_stream())
+    out = sites_section(args, M, torch, cloud, wl.n)
     line = {"metric": "same-manifold k-NN queries/sec (1M-pt torus, every site a query)",
             "value": out["k16"]["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "higher_is_better": True, "data": "synthetic",
@@ -1188,7 +1197,7 @@ def main():
     roof["traffic"] = _profiled_traffic(khash, wl.n, nq)
     roof["kernel_hash"] = khash
 
-    no_sort = k_sweep = prefix = batch = serving = cpu = None
+    no_sort = k_sweep = prefix = batch = serving = cpu = sites = None
     if not extras:
         e2e_s, agree = end_to_end()
     else:
@@ -1221,6 +1230,7 @@ def main():
                                                           "transitions": t_ / nq}),
                             "clocks": clk_k})
             del oi, od
+        sites = sites_section(args, M, torch, cloud, wl.n)
         # the host-buffer path after the background builds are done (host
         # copies and staging are timed, so the host cores should be free)
         for j in jobs.values():
@@ -1267,6 +1277,7 @@ def main():
             "l2_probe": args._l2,
             "no_sort": no_sort,
             "k_sweep": k_sweep,
+            "sites": sites,
             "prefix": prefix,
             "batch": batch,
             "serving": serving,

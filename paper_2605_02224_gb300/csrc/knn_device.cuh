@@ -674,7 +674,9 @@ struct PermList16 {
 #pragma unroll
     for (int step = 8; step >= 1; step >>= 1)
       if (col[slot(pos + step - 1) * 32] < c) pos += step;
-    if (pos >= k || col[slot(pos) * 32] == c) return;
+    // pos <= k - 1 because c < worst; slot() is below 16 whatever pos is, so
+    // no access leaves the thread's sixteen slots
+    if (col[slot(pos) * 32] == c) return;
     const int w = slot(k - 1);  // the dropped key's slot (or a pad's)
     col[w * 32] = c;
     // positions pos..k-2 move up by one, w goes to pos, k..15 stay

@@ -43,6 +43,14 @@ def test_query_kernel_name_matches_the_dispatch():
     assert bench._query_kernel_name(0, 20, 0) == "knn_plain_smem_kernel<256, 1, 0>"
     assert bench._query_kernel_name(0, 33, 0) == "knn_plain_smem_kernel<128, 2, 0>"
     assert bench._query_kernel_name(1, 128, 2) == "knn_plain_smem_kernel<64, 4, 0>"
+    # one warp per query from k = 48 by default, and for 32 lanes in shared memory
+    hdr = _read("knn_kernels.h")
+    assert f"constexpr int kWarpMinK = {bench.WARP_MIN_K};" in hdr
+    assert "int default_lanes(int k) { return k >= kWarpMinK ? 32 : 1; }" in _read("knn_plain.cu")
+    assert bench._query_kernel_name(0, 100, 0) == "knn_plain_warp_kernel<128>"
+    assert bench._query_kernel_name(0, 48, 0) == "knn_plain_warp_kernel<64>"
+    assert bench._query_kernel_name(32, 16, 2) == "knn_plain_warp_kernel<32>"
+    assert bench._query_kernel_name(0, 47, 0) == "knn_plain_smem_kernel<128, 2, 0>"
     assert bench._query_kernel_name(1, 16, 1) == "knn_plain_thread_kernel"
     assert bench._query_kernel_name(8, 16, 0).startswith("knn_plain_kernel<8")
 
