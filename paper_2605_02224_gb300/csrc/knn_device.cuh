@@ -781,14 +781,34 @@ __device__ __forceinline__ void knn_query_smem(const CloudDev& C, float qx, floa
   }
   // the output row is addressed only now, from its 32-bit index (fewer
   // registers held through the loop); streaming stores, so that the rows
-  // written do not push successor entries out of L2
+  // written do not push successor entries out of L2; four values per
+  // 16-byte store when k is a multiple of 4 and both arrays are 16-byte
+  // aligned (then every row is), else one value per store
   int32_t* oi = out_idx + (int64_t)row * k;
   float* od = out_d2 + (int64_t)row * k;
-  for (int p = 0; p < k; ++p) {
-    const bool real = p < N.cnt;
-    const uint64_t key = real ? N.key_at(p) : 0ull;
-    __stcs(oi + p, real ? (int32_t)(uint32_t)key : -1);
-    __stcs(od + p, real ? __uint_as_float((uint32_t)(key >> 32)) : __int_as_float(0x7f800000));
+  const bool vec = ((k & 3) == 0) &&
+                   ((((uintptr_t)out_idx) | ((uintptr_t)out_d2)) & 15) == 0;
+  if (vec) {
+    for (int p = 0; p < k; p += 4) {
+      int iv[4];
+      float dv[4];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const bool real = p + t < N.cnt;
+        const uint64_t key = real ? N.key_at(p + t) : 0ull;
+        iv[t] = real ? (int32_t)(uint32_t)key : -1;
+        dv[t] = real ? __uint_as_float((uint32_t)(key >> 32)) : __int_as_float(0x7f800000);
+      }
+      __stcs(reinterpret_cast<int4*>(oi + p), make_int4(iv[0], iv[1], iv[2], iv[3]));
+      __stcs(reinterpret_cast<float4*>(od + p), make_float4(dv[0], dv[1], dv[2], dv[3]));
+    }
+  } else {
+    for (int p = 0; p < k; ++p) {
+      const bool real = p < N.cnt;
+      const uint64_t key = real ? N.key_at(p) : 0ull;
+      __stcs(oi + p, real ? (int32_t)(uint32_t)key : -1);
+      __stcs(od + p, real ? __uint_as_float((uint32_t)(key >> 32)) : __int_as_float(0x7f800000));
+    }
   }
 }
 

@@ -372,3 +372,26 @@ def test_large_torus_full_size_sampled():
     hi, hd = c.knn_host(wl.queries[:300000], wl.k)
     assert np.array_equal(hi, idx[:300000]) and np.array_equal(hd, d2[:300000])
     c.close()
+
+
+def test_output_rows_unaligned_and_k_not_multiple_of_4():
+    """Rows are written four values per 16-byte store only when k is a
+    multiple of 4 and both output arrays are 16-byte aligned; outputs that
+    start 4 bytes into an allocation, and k = 10, take one value per store.
+    Every combination gives the same rows."""
+    import torch
+    wl = W.small_sphere(nq=3000)
+    c = Cloud.build(wl.points, wl.order).upload()
+    q = torch.from_numpy(wl.queries).cuda()
+    nq = wl.nq
+    for k in (16, 10, 8, 4):
+        ref_i, ref_d = c.knn(q, k)
+        base_i = torch.full((nq * k + 1,), -7, dtype=torch.int32, device="cuda")
+        base_d = torch.full((nq * k + 1,), -7.0, dtype=torch.float32, device="cuda")
+        oi, od = base_i[1:], base_d[1:]          # 4 bytes past a 256-byte boundary
+        s = torch.cuda.current_stream().cuda_stream
+        M.mknn_knn(c.handle, q, nq, 3, k, None, 0, oi, od, s)
+        torch.cuda.synchronize()
+        assert torch.equal(oi.view(nq, k), ref_i) and torch.equal(od.view(nq, k), ref_d), k
+        assert int(base_i[0]) == -7 and float(base_d[0]) == -7.0   # nothing written before
+    c.close()
