@@ -356,8 +356,9 @@ typedef struct {
 typedef struct {
   int32_t lanes;          /* 0 = tuned per request, else 1, 4, 8, 16 or 32 for all */
   int32_t sort;           /* 0 = sort requests with >= 4096 queries, 1 = all, -1 = none */
-  int32_t item_rounds;    /* rounds of the group width per work item (0 = 8,
-                             fewer for a plan too small to fill the GPU) */
+  int32_t item_rounds;    /* rounds of the group width per work item (0 = for one
+                             lane 8, fewer for a plan too small to fill the
+                             GPU; for groups of lanes 1) */
   int32_t blocks_per_sm;  /* 0 = occupancy limit */
   int32_t graph;          /* 0 = capture a CUDA graph (default), -1 = plain launches */
   int32_t placement;      /* with lanes set: 0 = that width's default, 1 = registers,

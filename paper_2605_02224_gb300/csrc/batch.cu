@@ -568,7 +568,8 @@ mknn_status mknn_batch_create(const mknn_batch_req* reqs, int32_t nreq,
   for (int r = 0; r < nreq; ++r) req_k[r] = reqs[r].k;
   for (int r : orderq) {
     const int v = variant_index(b->lanes[r], reqs[r].k, b->placement[r]);
-    const int per = item_queries(b->lanes[r], rounds);
+    const int per = item_queries(
+        b->lanes[r], o.item_rounds > 0 ? o.item_rounds : plan_item_rounds(b->lanes[r], rounds));
     for (int64_t s0 = 0; s0 < reqs[r].nq; s0 += per)
       items.push_back(Item{r, (int32_t)s0, (int32_t)std::min<int64_t>(reqs[r].nq, s0 + per), v});
   }

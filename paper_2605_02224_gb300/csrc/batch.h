@@ -41,6 +41,13 @@ struct Item {
 int variant_index(int lanes, int k, int placement);
 // Queries per work item for the given lanes and rounds per item.
 inline int item_queries(int lanes, int rounds) { return (32 / lanes) * rounds; }
+// Rounds per item a plan uses: `rounds` for one lane per query, one for a
+// group of lanes. A warp answers its item's queries one group-round after
+// another, so with groups (used for clouds with hub rows, where a few
+// queries scan lists of tens of thousands of entries) one slow query would
+// hold up the rest of its item: on a 322k-site planar-patches cloud a plan
+// of 32-lane items of 8 queries took 9.2 ms, of one query 3.2 ms.
+inline int plan_item_rounds(int lanes, int rounds) { return lanes > 1 ? 1 : rounds; }
 // Rounds per item for a launch whose requests need `warp_rounds` warp
 // rounds in all (sum over requests of ceil(nq * lanes / 32)): 8, or fewer
 // when that would leave too few items to keep every SM's warps busy (a

@@ -288,7 +288,7 @@ void mknn_server::launch(Slot& sl, std::vector<uint64_t>& tickets, size_t off, s
                      (int32_t*)(dbase + R.idx_off), (float*)(dbase + R.d2_off), c->d_err, q.k,
                      q.m ? q.m : (int32_t)c->n, (const float4*)cd.ent};
       const int v = variant_index(lanes[i], q.k, placement[i]);
-      const int per = item_queries(lanes[i], rounds);
+      const int per = item_queries(lanes[i], plan_item_rounds(lanes[i], rounds));
       req_k[i] = q.k;
       for (int64_t b0 = 0; b0 < q.nq; b0 += per)
         items.push_back(Item{i, (int32_t)b0, (int32_t)std::min<int64_t>(q.nq, b0 + per), v});
