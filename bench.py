@@ -100,13 +100,14 @@ def _peaks():
 WARP_MIN_K = 48   # from this k the library's default is one warp per query
 
 
-def _query_kernel_name(lanes: int, k: int, placement: int) -> str:
+def _query_kernel_name(lanes: int, k: int, placement: int, trees: bool = False) -> str:
     """The query kernel a plain launch with these options runs (its default:
     one lane per query with the list in shared memory, one warp per query
-    with the warp's list in shared memory from k = 48)."""
+    with the warp's list in shared memory from k = 48; the one-warp kernel's
+    second form walks the box trees of a cloud that has them)."""
     if (lanes == 0 and k >= WARP_MIN_K) or (lanes == 32 and placement in (0, 2)):
         kc = 32 if k <= 32 else (64 if k <= 64 else 128)
-        return f"knn_plain_warp_kernel<{kc}>"
+        return f"knn_plain_warp_kernel<{kc}, {'true' if trees else 'false'}>"
     if lanes in (0, 1) and placement in (0, 2):
         threads, words = (256, 1) if k <= 32 else ((128, 2) if k <= 64 else (64, 4))
         kind = 8 if k <= 8 else (16 if k <= 16 else 0)
@@ -616,20 +617,30 @@ def serving_section(args, M, torch, built=None):
 # library's plans pick them (placement 2: shared memory, 1: registers)
 _PLAN_VARIANTS = [(4, 1, 1), (4, 2, 1), (4, 4, 1), (8, 1, 1), (8, 2, 1), (8, 4, 1), (8, 8, 1),
                   (16, 1, 1), (16, 2, 1), (16, 4, 1), (32, 1, 1), (32, 2, 1), (1, 64, 2),
-                  (16, 8, 1), (32, 4, 1), (1, 128, 2), (32, 1, 2), (32, 2, 2), (32, 4, 2)]
+                  (16, 8, 1), (32, 4, 1), (1, 128, 2), (32, 1, 2), (32, 2, 2), (32, 4, 2),
+                  (32, 1, 2), (32, 2, 2), (32, 4, 2)]
+# index of the first one-warp variant with box trees (the last three entries)
+_TREE_VARIANT32 = 19
 
 
-def _plan_launches(lanes, reqs, placement=None) -> int:
+def _plan_launches(lanes, reqs, placement=None, trees=None) -> int:
     """Kernels one plan replay launches: the locality sort's five per request
     of at least 4096 queries, and one persistent kernel per variant present
-    (the fewest slots per lane that hold the request's k)."""
+    (the fewest slots per lane that hold the request's k; a one-warp
+    variant has a second form for clouds with box trees, trees[i])."""
     variants = set()
     placement = placement if placement is not None else [2 if g in (1, 32) else 1 for g in lanes]
-    for g, p, r in zip(lanes.tolist() if hasattr(lanes, "tolist") else lanes,
-                       placement.tolist() if hasattr(placement, "tolist") else placement, reqs):
+    trees = trees if trees is not None else [False] * len(reqs)
+    for g, p, r, t in zip(lanes.tolist() if hasattr(lanes, "tolist") else lanes,
+                          placement.tolist() if hasattr(placement, "tolist") else placement,
+                          reqs, trees):
         lst = 2 if g == 1 else (p if g == 32 else 1)
-        fits = [v for v in _PLAN_VARIANTS if v[0] == g and v[2] == lst and v[0] * v[1] >= r["k"]]
-        variants.add(min(fits, key=lambda v: v[1]))
+        fits = [i for i, v in enumerate(_PLAN_VARIANTS[:_TREE_VARIANT32])
+                if v[0] == g and v[2] == lst and v[0] * v[1] >= r["k"]]
+        v = min(fits, key=lambda i: _PLAN_VARIANTS[i][1])
+        if t and g == 32 and lst == 2:
+            v += _TREE_VARIANT32 - 16
+        variants.add(v)
     return len(variants) + 5 * sum(1 for r in reqs if r["nq"] >= 4096)
 
 
@@ -719,7 +730,9 @@ def batch_section(args, M, torch, built=None):
                                     for l, p in set(zip(lanes.tolist(), placement.tolist()))},
                    "tune_seconds": tune_s,
                    "build_seconds_max": build_s if build_s is not None else "cached"},
-        "gpu_launches_per_step": _plan_launches(lanes, reqs, placement),
+        "gpu_launches_per_step": _plan_launches(lanes, reqs, placement,
+                                                [M.mknn_cloud_trees(r["cloud"])[0] > 0
+                                                 for r in reqs]),
         "clocks": clk,
     }
 

@@ -121,7 +121,14 @@ mknn_status mknn_cloud_from_table(const float* xyz_ranked, int64_t n, const int6
  * respect to the host (the copies complete before return). Device bytes:
  * 24 n + 20 E plus a few words of status (a dynamic cloud also reserves
  * room for appends: a quarter more sites and entries, at least 4096 sites
- * and 65536 entries). Errors: ENOMEM, ECUDA. */
+ * and 65536 entries). A cloud without appends whose longest successor list
+ * has 4096 entries or more also gets a box tree over every list of 256
+ * entries or more (an index for the one-warp
+ * query kernel, which searches such a list through its tree instead of
+ * reading it in rank order, with the same result; Algorithms 1-2 need
+ * only the entries that can be strictly closer than the current site, or
+ * below the k-th key): 4 n bytes plus about 17 bytes per entry of those
+ * lists (see mknn_cloud_trees). Errors: ENOMEM, ECUDA. */
 mknn_status mknn_cloud_upload(mknn_cloud* cloud, mknn_stream_t stream);
 
 /* mknn_cloud_append: inserts `count` new points after the existing ones,
@@ -168,6 +175,12 @@ mknn_status mknn_cloud_free(mknn_cloud* cloud);
 /* Sizes: n, E (total successor entries) and device bytes (0 if not
  * uploaded). Any output pointer may be NULL. */
 mknn_status mknn_cloud_info(const mknn_cloud* cloud, int64_t* n, int64_t* E, size_t* dev_bytes);
+
+/* Box trees of the device copy (mknn_cloud_upload): number of trees and
+ * the entries of the lists they cover (0 and 0 before upload, for a cloud
+ * built for appends, and when no list has 4096 entries). Either output may
+ * be NULL. The paper has no such index: it reads every list in rank order. */
+mknn_status mknn_cloud_trees(const mknn_cloud* cloud, int64_t* trees, int64_t* entries);
 
 /* order_out host int64[n]: rank -> input index. */
 mknn_status mknn_cloud_order(const mknn_cloud* cloud, int64_t* order_out);
@@ -356,9 +369,7 @@ typedef struct {
 typedef struct {
   int32_t lanes;          /* 0 = tuned per request, else 1, 4, 8, 16 or 32 for all */
   int32_t sort;           /* 0 = sort requests with >= 4096 queries, 1 = all, -1 = none */
-  int32_t item_rounds;    /* rounds of the group width per work item (0 = for one
-                             lane 8, fewer for a plan too small to fill the
-                             GPU; for groups of lanes 1) */
+  int32_t item_rounds;    /* rounds of the group width per work item (0 = 1) */
   int32_t blocks_per_sm;  /* 0 = occupancy limit */
   int32_t graph;          /* 0 = capture a CUDA graph (default), -1 = plain launches */
   int32_t placement;      /* with lanes set: 0 = that width's default, 1 = registers,

@@ -57,6 +57,10 @@ class Cloud:
     def device_bytes(self) -> int:
         return M.mknn_cloud_info(self.handle)[2]
 
+    def trees(self):
+        """(box trees on the device copy, entries of the lists they cover)."""
+        return M.mknn_cloud_trees(self.handle)
+
     def knn(self, q, k: int, m=None, stream: int = 0, **opt):
         """q: torch CUDA tensor (nq, 3 or 4) float32; m: None, int or int32
         CUDA tensor (nq,). Returns (idx int32 (nq,k), d2 float32 (nq,k))."""

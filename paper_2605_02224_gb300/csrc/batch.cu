@@ -49,13 +49,17 @@ constexpr VariantDesc kVariants[] = {{4, 1, 1},  {4, 2, 1},  {4, 4, 1},  {8, 1, 
                                      {8, 2, 1},  {8, 4, 1},  {8, 8, 1},  {16, 1, 1},
                                      {16, 2, 1}, {16, 4, 1}, {32, 1, 1}, {32, 2, 1},
                                      {1, 64, 2}, {16, 8, 1}, {32, 4, 1}, {1, 128, 2},
-                                     {32, 1, 2}, {32, 2, 2}, {32, 4, 2}};
+                                     {32, 1, 2}, {32, 2, 2}, {32, 4, 2}, {32, 1, 2},
+                                     {32, 2, 2}, {32, 4, 2}};
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 static_assert(kVariants[kSmemVariant].g == 1 && kVariants[kSmemVariant128].g == 1,
               "one-lane variant indices");
 static_assert(kVariants[kWarpVariant32].g == 32 && kVariants[kWarpVariant32].list == 2 &&
                   kVariants[kWarpVariant32 + 2].s == 4,
               "warp variant indices");
+static_assert(kVariants[kTreeVariant32].g == 32 && kVariants[kTreeVariant32].list == 2 &&
+                  kVariants[kTreeVariant32 + 2].s == 4 && kTreeVariant32 + 3 == kNumVariants,
+              "tree variant indices");
 
 }  // namespace
 
@@ -173,14 +177,14 @@ __global__ void __launch_bounds__(THREADS, THREADS == 256 ? 5 : 1) knn_batch_sme
 // One warp per query, its candidate list in shared memory (KC keys per
 // warp, static): the warp takes an item and answers its queries one after
 // another.
-template <int KC>
+template <int KC, bool TREES>
 __global__ void __launch_bounds__(kThreads) knn_batch_warp_kernel(const ReqDev* __restrict__ reqs,
                                                                   const Item* __restrict__ items,
                                                                   int nitems,
                                                                   int* __restrict__ next,
                                                                   int kcap) {
   (void)kcap;
-  __shared__ uint64_t lists[kThreads / 32][KC];
+  __shared__ uint64_t lists[kThreads / 32][kWarpListWords(KC)];
   const int warp = (int)(threadIdx.x >> 5);
   const uint32_t lane = threadIdx.x & 31u;
   for (;;) {
@@ -190,7 +194,8 @@ __global__ void __launch_bounds__(kThreads) knn_batch_warp_kernel(const ReqDev* 
     if (it >= nitems) return;
     const Item w = items[it];
     const ReqDev& R = reqs[w.req];
-    const CloudDev C{R.pts, R.rows, R.succ, R.n, R.ent};
+    const CloudDev C{R.pts,    R.rows,     R.succ,    R.n,       R.ent,
+                     R.hub_of, R.hub_desc, R.hub_ent, R.hub_node};
     for (int i = w.begin; i < w.end; ++i) {
       const int64_t qi = R.perm ? (int64_t)__ldg(R.perm + i) : (int64_t)i;
       const float* qp = R.q + qi * R.q_stride;
@@ -204,7 +209,8 @@ __global__ void __launch_bounds__(kThreads) knn_batch_warp_kernel(const ReqDev* 
         if (lane == 0) atomicOr(R.err, 1);
         continue;
       }
-      knn_query_warp<KC>(C, qx, qy, qz, R.k, m, lists[warp], R.out_idx, R.out_d2, (int32_t)qi);
+      knn_query_warp<KC, TREES>(C, qx, qy, qz, R.k, m, lists[warp], R.out_idx, R.out_d2,
+                                (int32_t)qi);
     }
     __syncwarp();
   }
@@ -254,12 +260,6 @@ int fill_lanes(int64_t nq, int k) {
   while (lanes < 32 && nq * lanes < target) lanes <<= 1;
   if (lanes == 2) lanes = 4;  // no two-lane variant
   return lanes;
-}
-
-int auto_item_rounds(int64_t warp_rounds) {
-  // two items per resident warp (40 per SM at 48 registers) before rounds grow
-  const int64_t target = (int64_t)num_sms() * 40 * 2;
-  return (int)std::max<int64_t>(1, std::min<int64_t>(8, warp_rounds / target));
 }
 
 Mode choose_mode(int k, int64_t n, int hub, int64_t nq) {
@@ -318,9 +318,12 @@ const void* variant_kernel(int variant, int threads) {
     case 11: return (const void*)knn_batch_group_kernel<32, 2>;
     case 13: return (const void*)knn_batch_group_kernel<16, 8>;
     case 14: return (const void*)knn_batch_group_kernel<32, 4>;
-    case kWarpVariant32: return (const void*)knn_batch_warp_kernel<32>;
-    case kWarpVariant32 + 1: return (const void*)knn_batch_warp_kernel<64>;
-    case kWarpVariant32 + 2: return (const void*)knn_batch_warp_kernel<128>;
+    case kWarpVariant32: return (const void*)knn_batch_warp_kernel<32, false>;
+    case kWarpVariant32 + 1: return (const void*)knn_batch_warp_kernel<64, false>;
+    case kWarpVariant32 + 2: return (const void*)knn_batch_warp_kernel<128, false>;
+    case kTreeVariant32: return (const void*)knn_batch_warp_kernel<32, true>;
+    case kTreeVariant32 + 1: return (const void*)knn_batch_warp_kernel<64, true>;
+    case kTreeVariant32 + 2: return (const void*)knn_batch_warp_kernel<128, true>;
     case kSmemVariant:
       return threads == 256 ? (const void*)knn_batch_smem_kernel<256, 1>
                             : (const void*)knn_batch_smem_kernel<128, 2>;
@@ -367,13 +370,26 @@ cudaError_t launch_batch_kernel(const ReqDev* d_reqs, const Item* d_items, int n
 
 std::vector<Segment> make_segments(std::vector<Item>& items, int blocks_per_sm,
                                    const std::vector<int>& req_k) {
+  // one-lane items by list class (8, 16, 32, 64 slots): a launch's shared
+  // memory is sized for its largest list, and a list of 8 slots in a block
+  // sized for 32 would cut the resident threads by two fifths (non-hub
+  // requests of the batching workload: 99 ms in four one-lane segments
+  // against 107 ms in one)
   auto rank = [](int v) { return is_smem_variant(v) ? v - 100 : v; };
-  std::stable_sort(items.begin(), items.end(),
-                   [&](const Item& a, const Item& c) { return rank(a.variant) < rank(c.variant); });
+  auto cls = [&](const Item& a) {
+    if (!is_smem_variant(a.variant)) return 0;
+    const int slots = list_slots(req_k[a.req]);
+    return slots <= 8 ? 0 : (slots <= 16 ? 1 : (slots <= 32 ? 2 : 3));
+  };
+  std::stable_sort(items.begin(), items.end(), [&](const Item& a, const Item& c) {
+    return rank(a.variant) != rank(c.variant) ? rank(a.variant) < rank(c.variant) : cls(a) < cls(c);
+  });
   std::vector<Segment> segs;
   for (int i = 0; i < (int)items.size();) {
     int j = i;
-    while (j < (int)items.size() && items[j].variant == items[i].variant) ++j;
+    while (j < (int)items.size() && items[j].variant == items[i].variant &&
+           cls(items[j]) == cls(items[i]))
+      ++j;
     int kcap = 0;
     for (int t = i; t < j; ++t) kcap = std::max(kcap, list_slots(req_k[items[t].req]));
     Segment g;
@@ -541,7 +557,9 @@ mknn_status mknn_batch_create(const mknn_batch_req* reqs, int32_t nreq,
     const CloudDevHost cd = R.cloud->dev();
     rd[r] = ReqDev{(const float4*)cd.pts, cd.rows,   cd.succ, cd.n,  R.q_stride,
                    R.q,                   R.m,       nullptr, R.out_idx,
-                   R.out_d2,              R.cloud->d_err, R.k, ms, (const float4*)cd.ent};
+                   R.out_d2,              R.cloud->d_err, R.k, ms, (const float4*)cd.ent,
+                   cd.hub_of, (const int4*)cd.hub_desc, (const float4*)cd.hub_ent,
+                   (const float4*)cd.hub_node};
     cost[r] = (double)R.k * std::log2((double)R.cloud->n + 2.0);
     b->total_queries += R.nq;
   }
@@ -560,16 +578,14 @@ mknn_status mknn_batch_create(const mknn_batch_req* reqs, int32_t nreq,
   std::vector<int> orderq(nreq);
   for (int r = 0; r < nreq; ++r) orderq[r] = r;
   std::stable_sort(orderq.begin(), orderq.end(), [&](int a, int c) { return cost[a] > cost[c]; });
-  int64_t warp_rounds = 0;
-  for (int r = 0; r < nreq; ++r) warp_rounds += (reqs[r].nq * b->lanes[r] + 31) / 32;
-  const int rounds = o.item_rounds > 0 ? o.item_rounds : auto_item_rounds(warp_rounds);
+  const int rounds = o.item_rounds > 0 ? o.item_rounds : kItemRounds;
   std::vector<Item> items;
   std::vector<int> req_k(nreq);
   for (int r = 0; r < nreq; ++r) req_k[r] = reqs[r].k;
   for (int r : orderq) {
-    const int v = variant_index(b->lanes[r], reqs[r].k, b->placement[r]);
-    const int per = item_queries(
-        b->lanes[r], o.item_rounds > 0 ? o.item_rounds : plan_item_rounds(b->lanes[r], rounds));
+    const int v = with_trees(variant_index(b->lanes[r], reqs[r].k, b->placement[r]),
+                             reqs[r].cloud->d_hub_of != nullptr);
+    const int per = item_queries(b->lanes[r], rounds);
     for (int64_t s0 = 0; s0 < reqs[r].nq; s0 += per)
       items.push_back(Item{r, (int32_t)s0, (int32_t)std::min<int64_t>(reqs[r].nq, s0 + per), v});
   }

@@ -24,6 +24,11 @@ struct ReqDev {
   int32_t k;
   int32_t m_scalar;
   const float4* ent;   // the cloud's successor entries with sites inlined
+  // the cloud's box trees over its long lists (read by the one-warp variant)
+  const int32_t* hub_of;
+  const int4* hub_desc;
+  const float4* hub_ent;
+  const float4* hub_node;
 };
 
 // Queries per request below this bound: a lane's query index plus its
@@ -41,18 +46,15 @@ struct Item {
 int variant_index(int lanes, int k, int placement);
 // Queries per work item for the given lanes and rounds per item.
 inline int item_queries(int lanes, int rounds) { return (32 / lanes) * rounds; }
-// Rounds per item a plan uses: `rounds` for one lane per query, one for a
-// group of lanes. A warp answers its item's queries one group-round after
-// another, so with groups (used for clouds with hub rows, where a few
-// queries scan lists of tens of thousands of entries) one slow query would
-// hold up the rest of its item: on a 322k-site planar-patches cloud a plan
-// of 32-lane items of 8 queries took 9.2 ms, of one query 3.2 ms.
-inline int plan_item_rounds(int lanes, int rounds) { return lanes > 1 ? 1 : rounds; }
-// Rounds per item for a launch whose requests need `warp_rounds` warp
-// rounds in all (sum over requests of ceil(nq * lanes / 32)): 8, or fewer
-// when that would leave too few items to keep every SM's warps busy (a
-// small pack is cut finer so its latency stays that of a plain launch).
-int auto_item_rounds(int64_t warp_rounds);
+// Rounds per work item (a warp answers its item's queries one round after
+// another): one. Longer items hold up the end of a persistent launch and,
+// with groups of lanes on clouds with hub rows, let one slow query hold up
+// the rest of its item. On the 64-cloud batching workload (57.6M queries)
+// the plan took 233 / 240 / 248 ms with items of 1 / 2 / 4 rounds and 276
+// ms with the earlier 8 for one lane per query (one plain launch per cloud:
+// 240 ms); on a 322k-site planar-patches cloud 32-lane items of 8 queries
+// took 9.2 ms, of one query 3.2 ms.
+constexpr int kItemRounds = 1;
 
 // Variant indices of the one-lane shared-memory kernels (k <= 64, k <= 128).
 constexpr int kSmemVariant = 12;
@@ -61,6 +63,18 @@ inline bool is_smem_variant(int v) { return v == kSmemVariant || v == kSmemVaria
 // Variant indices of the one-warp-per-query kernels with the list in shared
 // memory: kWarpVariant32 + 0, 1, 2 for k <= 32, 64, 128.
 constexpr int kWarpVariant32 = 16;
+// The same three for clouds with box trees over their long lists (the
+// walk's code would slow the scan of clouds without them):
+// kTreeVariant32 + 0, 1, 2.
+constexpr int kTreeVariant32 = 19;
+// The variant a request runs: a one-warp variant turns into its tree form
+// when the request's cloud has trees. variant_index never returns the tree
+// forms (it picks the first of equal variants).
+inline int with_trees(int v, bool trees) {
+  return (trees && v >= kWarpVariant32 && v < kWarpVariant32 + 3)
+             ? v + (kTreeVariant32 - kWarpVariant32)
+             : v;
+}
 
 // Lanes per query and where the candidate list lives (2 = shared memory,
 // 1 = registers).

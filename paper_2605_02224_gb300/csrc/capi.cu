@@ -17,6 +17,7 @@
 #include "knn_kernels.h"
 #include "predicates.h"
 #include "batch.h"
+#include "hub_index.h"
 
 namespace mknn {
 
@@ -81,8 +82,15 @@ void free_device(mknn_cloud* c) {
     cudaFree(c->d_succ);
     cudaFree(c->d_ent);
     cudaFree(c->d_err);
+    cudaFree(c->d_hub_of);
+    cudaFree(c->d_hub_desc);
+    cudaFree(c->d_hub_ent);
+    cudaFree(c->d_hub_node);
     cudaSetDevice(cur);
   }
+  c->d_hub_of = nullptr;
+  c->d_hub_desc = c->d_hub_ent = c->d_hub_node = nullptr;
+  c->hub_trees = c->hub_entries = 0;
   c->d_pts = nullptr;
   c->d_ent = nullptr;
   c->pts_cap = c->ent_cap = c->ent_top = 0;
@@ -338,10 +346,49 @@ mknn_status mknn_cloud_upload(mknn_cloud* c, mknn_stream_t stream) {
     free_device(c);
     return cuda_fail(e, "upload");
   }
+  // box trees over the long lists (a dynamic cloud's lists change: none)
+  size_t b_hub = 0;
+  if (!dyn && E > 0) {
+    HubIndex H;
+    try {
+      build_hub_index(n, c->xyz.data(), c->rowp.data(), c->succ.data(), kHubMinRow,
+                      kHubMinLongest, &H);
+    } catch (const std::bad_alloc&) {
+      free_device(c);
+      return fail(MKNN_ENOMEM, "host allocation failed");
+    }
+    if (H.hubs() > 0) {
+      const size_t b_of = H.hub_of.size() * 4, b_desc = H.desc.size() * 4,
+                   b_hent = H.ent.size() * 4, b_node = H.node.size() * 4;
+      if ((e = cudaMalloc((void**)&c->d_hub_of, b_of)) != cudaSuccess ||
+          (e = cudaMalloc(&c->d_hub_desc, b_desc)) != cudaSuccess ||
+          (e = cudaMalloc(&c->d_hub_ent, b_hent)) != cudaSuccess ||
+          (e = cudaMalloc(&c->d_hub_node, b_node)) != cudaSuccess) {
+        cudaGetLastError();
+        free_device(c);
+        return fail(MKNN_ENOMEM, std::string("device allocation failed: ") + cudaGetErrorString(e));
+      }
+      if ((e = cudaMemcpyAsync(c->d_hub_of, H.hub_of.data(), b_of, cudaMemcpyHostToDevice, s)) !=
+              cudaSuccess ||
+          (e = cudaMemcpyAsync(c->d_hub_desc, H.desc.data(), b_desc, cudaMemcpyHostToDevice,
+                               s)) != cudaSuccess ||
+          (e = cudaMemcpyAsync(c->d_hub_ent, H.ent.data(), b_hent, cudaMemcpyHostToDevice, s)) !=
+              cudaSuccess ||
+          (e = cudaMemcpyAsync(c->d_hub_node, H.node.data(), b_node, cudaMemcpyHostToDevice,
+                               s)) != cudaSuccess ||
+          (e = cudaStreamSynchronize(s)) != cudaSuccess) {  // before H goes
+        free_device(c);
+        return cuda_fail(e, "upload");
+      }
+      b_hub = b_of + b_desc + b_hent + b_node;
+      c->hub_trees = H.hubs();
+      for (int64_t h = 0; h < H.hubs(); ++h) c->hub_entries += H.desc[4 * h + 1];
+    }
+  }
   c->pts_cap = pcap;
   c->ent_cap = ecap;
   c->ent_top = E + slack * n;
-  c->dev_bytes = b_pts + b_rows + b_succ + b_ent + 256;
+  c->dev_bytes = b_pts + b_rows + b_succ + b_ent + 256 + b_hub;
   return MKNN_OK;
 }
 
@@ -366,6 +413,13 @@ mknn_status mknn_cloud_info(const mknn_cloud* c, int64_t* n, int64_t* E, size_t*
   if (n) *n = c->n;
   if (E) *E = c->E();
   if (dev_bytes) *dev_bytes = c->dev_bytes;
+  return MKNN_OK;
+}
+
+mknn_status mknn_cloud_trees(const mknn_cloud* c, int64_t* trees, int64_t* entries) {
+  if (!c) return fail(MKNN_EINVAL, "cloud is NULL");
+  if (trees) *trees = c->hub_trees;
+  if (entries) *entries = c->hub_entries;
   return MKNN_OK;
 }
 

@@ -36,6 +36,12 @@ struct mknn_cloud {
   int32_t* d_succ = nullptr;     // [E]
   void* d_ent = nullptr;         // float4[E]: succ with the sites' coordinates inlined
   int32_t* d_err = nullptr;      // error flags
+  // box trees over the long lists of a static cloud (hub_index.h), or NULL
+  int32_t* d_hub_of = nullptr;   // [n]
+  void* d_hub_desc = nullptr;    // int4 per tree
+  void* d_hub_ent = nullptr;     // float4 per entry
+  void* d_hub_node = nullptr;    // two float4 per node
+  int64_t hub_trees = 0, hub_entries = 0;  // trees, and the entries of their lists
   size_t dev_bytes = 0;
   // device capacities: sites (d_pts, d_rows) and entries (d_succ, d_ent);
   // a dynamic cloud's rows live in an append-only arena: row i occupies
@@ -76,6 +82,10 @@ struct mknn_cloud {
     c.rows = d_rows;
     c.succ = d_succ;
     c.ent = d_ent;
+    c.hub_of = d_hub_of;
+    c.hub_desc = d_hub_desc;
+    c.hub_ent = d_hub_ent;
+    c.hub_node = d_hub_node;
     c.n = (int32_t)n;
     for (int i = 0; i < 3; ++i) {
       c.lo[i] = lo[i];

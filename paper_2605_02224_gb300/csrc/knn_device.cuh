@@ -30,6 +30,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "hub_index.h"
+
 namespace mknn {
 
 constexpr uint32_t kRankMask = 0x7fffffffu;
@@ -49,6 +51,16 @@ struct CloudDev {
   // succ with each entry's site inlined: (x, y, z, rank bits), one 16-byte
   // load per entry instead of an index load and a dependent point load
   const float4* __restrict__ ent;
+  // box trees over the long lists (NULL hub_of: none); read by the one-warp
+  // kernel only. hub_of[i]: the tree of site i's list or -1; hub_desc:
+  // (first entry, list length, first node, levels); hub_ent: the list's
+  // entries along a Morton curve in chunks of 32; hub_node: two float4 per
+  // node, (low corner, smallest rank's bits) and (high corner, largest
+  // rank's bits), levels stored from the chunks' boxes up
+  const int32_t* __restrict__ hub_of = nullptr;
+  const int4* __restrict__ hub_desc = nullptr;
+  const float4* __restrict__ hub_ent = nullptr;
+  const float4* __restrict__ hub_node = nullptr;
 };
 
 // Squared distance in float32, fixed operation order (no reassociation).
@@ -943,8 +955,170 @@ struct WarpList {
   }
 };
 
-// One query by one warp (every lane calls it with the same query).
+// Box trees over long lists (one warp; every lane passes the same arguments).
+
+// Node count of one level of a tree over len entries, and the level's
+// offset from the tree's first node (the chunks' level first).
+__device__ __forceinline__ void hub_level_of(int len, int level, int& off, int& cnt) {
+  int c = (len + 31) >> 5, o = 0;
+  for (int l = 0; l < level; ++l) {
+    o += c;
+    c = (c + 31) >> 5;
+  }
+  off = o;
+  cnt = c;
+}
+
+// Squared distance from q to the box [lo, hi] with sqd32's operations,
+// applied to per-axis gaps that are never larger in magnitude than the gap
+// to any point of the box. Subtraction, product and fused add are monotonic
+// under round-to-nearest, so the result is at most sqd32(q, p) for every
+// site p in the box: no rounding can make a box look farther than a site
+// inside it.
+__device__ __forceinline__ float box_sqd32(float qx, float qy, float qz, float4 lo, float4 hi) {
+  const float dx = qx < lo.x ? __fsub_rn(qx, lo.x) : (qx > hi.x ? __fsub_rn(qx, hi.x) : 0.f);
+  const float dy = qy < lo.y ? __fsub_rn(qy, lo.y) : (qy > hi.y ? __fsub_rn(qy, hi.y) : 0.f);
+  const float dz = qz < lo.z ? __fsub_rn(qz, lo.z) : (qz > hi.z ? __fsub_rn(qz, hi.z) : 0.f);
+  float d = __fmul_rn(dx, dx);
+  d = __fmaf_rn(dy, dy, d);
+  d = __fmaf_rn(dz, dz, d);
+  return d;
+}
+
+// Depth-first walk of tree D. The children of a node are tested one per
+// lane with keep(low, high) and the kept ones are entered in order; each is
+// tested again when entered, since the bounds tighten as chunks are
+// handled. A kept chunk (level 0) goes to leaf(chunk). Every decision is
+// the same in all lanes, so the warp stays converged. stack: 2 x
+// kHubMaxLevels words of the warp's shared memory.
+template <class Keep, class Leaf>
+__device__ __forceinline__ void hub_walk(const CloudDev& C, int4 D, int lane, uint32_t* stack,
+                                         Keep&& keep, Leaf&& leaf) {
+  const int len = D.y, node0 = D.z, top = D.w - 1;
+  // per level: the children not entered yet (pend) and the index of their
+  // first (first); every lane writes the same values
+  uint32_t* pend = stack;
+  uint32_t* first = stack + kHubMaxLevels;
+  int l = top, off, cnt;
+  hub_level_of(len, l, off, cnt);
+  bool kept = false;
+  if (lane < cnt) {
+    const int j = node0 + off + lane;
+    kept = keep(__ldg(C.hub_node + 2 * j), __ldg(C.hub_node + 2 * j + 1));
+  }
+  pend[l] = __ballot_sync(0xffffffffu, kept);
+  first[l] = 0;
+  for (;;) {
+    const uint32_t pm = pend[l];
+    if (pm == 0u) {
+      if (++l > top) break;
+      continue;
+    }
+    const int node = (int)first[l] + __ffs((int)pm) - 1;
+    pend[l] = pm & (pm - 1u);
+    hub_level_of(len, l, off, cnt);
+    const int j = node0 + off + node;
+    if (!keep(__ldg(C.hub_node + 2 * j), __ldg(C.hub_node + 2 * j + 1))) continue;
+    if (l == 0) {
+      leaf(node);
+      continue;
+    }
+    --l;
+    hub_level_of(len, l, off, cnt);
+    const int c = 32 * node + lane;
+    kept = false;
+    if (c < cnt) {
+      const int jc = node0 + off + c;
+      kept = keep(__ldg(C.hub_node + 2 * jc), __ldg(C.hub_node + 2 * jc + 1));
+    }
+    pend[l] = __ballot_sync(0xffffffffu, kept);
+    first[l] = (uint32_t)(32 * node);
+  }
+}
+
+// Algorithm 1's step on a list with a tree: the lowest rank below m whose
+// site is strictly closer than the current one (rank cur, squared distance
+// dcur) - the first such entry of the list in rank order - or -1; its
+// squared distance goes to bd. A box is skipped when its nearest point is
+// beyond the float32 distance above which strictly_closer says no, or its
+// smallest rank is not below m or below the best found.
+__device__ __forceinline__ int hub_first_closer(const CloudDev& C, int hub, float qx, float qy,
+                                                float qz, float dcur, int cur, int m, int lane,
+                                                uint32_t* stack, float& bd) {
+  const int4 D = __ldg(C.hub_desc + hub);
+  const float reach = dcur >= kTiny ? dcur * (1.f + kGuard) : 2.f * kTiny;
+  int best = 0x7fffffff;
+  float bestd = 0.f;
+  hub_walk(
+      C, D, lane, stack,
+      [&](float4 lo, float4 hi) {
+        const int r = __float_as_int(lo.w);
+        return r < m && r < best && !(box_sqd32(qx, qy, qz, lo, hi) > reach);
+      },
+      [&](int chunk) {
+        const float4 ps = __ldg(C.hub_ent + D.x + 32 * chunk + lane);
+        const int s = __float_as_int(ps.w);  // pads: 0x7fffffff, never below m
+        const float d = sqd32(qx, qy, qz, ps);
+        const bool cl = s < m && s < best && strictly_closer_at(C, qx, qy, qz, d, ps, dcur, cur);
+        const int low = __reduce_min_sync(0xffffffffu, cl ? s : 0x7fffffff);
+        if (low < best) {
+          const int w = __ffs((int)__ballot_sync(0xffffffffu, cl && s == low)) - 1;
+          best = low;
+          bestd = __shfl_sync(0xffffffffu, d, w);
+        }
+      });
+  bd = bestd;
+  return best == 0x7fffffff ? -1 : best;
+}
+
+// Algorithm 2's offer of a list with a tree: every entry below m whose key
+// is below the k-th key of N goes to N. A box is skipped when its nearest
+// point is farther than the k-th key's distance (the pad key's distance is
+// a NaN, which skips nothing) or its smallest rank is not below m. N ends
+// as after the scan in rank order: the k smallest keys of N and the list.
 template <int KC>
+__device__ __forceinline__ void hub_offer(const CloudDev& C, int hub, float qx, float qy,
+                                          float qz, int m, int k, WarpList<KC>& N, int lane,
+                                          uint32_t* stack) {
+  const int4 D = __ldg(C.hub_desc + hub);
+  hub_walk(
+      C, D, lane, stack,
+      [&](float4 lo, float4 hi) {
+        const float wd = __uint_as_float((uint32_t)(N.worst >> 32));
+        return __float_as_int(lo.w) < m && !(box_sqd32(qx, qy, qz, lo, hi) > wd);
+      },
+      [&](int chunk) {
+        const float4 ps = __ldg(C.hub_ent + D.x + 32 * chunk + lane);
+        const int s = __float_as_int(ps.w);
+        const float d = sqd32(qx, qy, qz, ps);
+        const uint64_t key = pack_key(d, (uint32_t)s);
+        const bool fresh = s < m && key < N.worst && !N.contains(key);
+        uint32_t b = __ballot_sync(0xffffffffu, fresh);
+        while (b) {
+          const int j = __ffs((int)b) - 1;
+          b &= b - 1;
+          const uint64_t c = __shfl_sync(0xffffffffu, key, j);
+          if (c < N.worst) N.insert(c, k, lane);
+        }
+      });
+}
+
+// Entries of a list with a tree that the descent reads in rank order before
+// it turns to the tree: the first strictly closer entry is often among the
+// first few (the low ranks are spread over the whole cloud), and a walk
+// that must prove its rank the lowest costs more than a chunk or two.
+constexpr int kHubScanFirst = 64;
+// 64-bit words of shared memory for one warp of knn_query_warp<KC>.
+__host__ __device__ constexpr int kWarpListWords(int kc) { return kc + kHubMaxLevels; }
+
+// One query by one warp (every lane calls it with the same query). With
+// TREES (a cloud whose hub_of is not NULL) a list with a box tree is
+// searched through the tree (after kHubScanFirst entries in the descent);
+// the result is the same as the scan's. The walk's code costs registers
+// and issue slots in the scan loop too, so clouds without trees run the
+// instantiation without it. list: the warp's kWarpListWords(KC) words of
+// shared memory (KC keys, then the tree walk's stack).
+template <int KC, bool TREES>
 __device__ __forceinline__ void knn_query_warp(const CloudDev& C, float qx, float qy, float qz,
                                                int k, int m, uint64_t* list,
                                                int32_t* __restrict__ out_idx,
@@ -956,45 +1130,74 @@ __device__ __forceinline__ void knn_query_warp(const CloudDev& C, float qx, floa
   N.insert(pack_key(dcur, 0u), k, lane);
   int cur = 0;  // the descent's current site, -1 once it is over
   int2 rr = __ldg(C.rows);
+  int hub = -1;  // the current list's tree, or -1
+  if constexpr (TREES) hub = __ldg(C.hub_of);
   int base = rr.x, end = rr.y;
   for (;;) {
-    const int e = base + lane;
-    const bool valid = e < end;
-    float4 ps = make_float4(0.f, 0.f, 0.f, __int_as_float(0x7fffffff));
-    if (valid) ps = __ldg(C.ent + e);
-    const int s = __float_as_int(ps.w);
-    const bool inr = valid && s < m;  // rows ascend: past the first s >= m nothing is
-    const float d = sqd32(qx, qy, qz, ps);
-    const uint64_t key = pack_key(d, (uint32_t)s);
-    const bool row_done = __any_sync(0xffffffffu, valid && !inr) || base + 32 >= end;
-    if (cur >= 0) {
-      const bool cl = inr && strictly_closer_at(C, qx, qy, qz, d, ps, dcur, cur);
-      const uint32_t b = __ballot_sync(0xffffffffu, cl);
-      if (b) {
-        const int w = __ffs((int)b) - 1;
-        cur = __shfl_sync(0xffffffffu, s, w);
-        dcur = __shfl_sync(0xffffffffu, d, w);
-        const uint64_t kw = __shfl_sync(0xffffffffu, key, w);
-        if (kw < N.worst) N.insert(kw, k, lane);
-        rr = __ldg(C.rows + cur);
-        base = rr.x;
-        end = rr.y;
+    bool via_tree = false;
+    if constexpr (TREES) via_tree = hub >= 0 && (cur < 0 || base - rr.x >= kHubScanFirst);
+    if (via_tree) {
+      if constexpr (TREES) {  // the list through its tree
+        if (cur >= 0) {
+          float bd;
+          const int b = hub_first_closer(C, hub, qx, qy, qz, dcur, cur, m, lane,
+                                         (uint32_t*)(list + KC), bd);
+          if (b >= 0) {
+            cur = b;
+            dcur = bd;
+            const uint64_t kb = pack_key(bd, (uint32_t)b);
+            if (kb < N.worst) N.insert(kb, k, lane);
+            rr = __ldg(C.rows + cur);
+            base = rr.x;
+            end = rr.y;
+            hub = __ldg(C.hub_of + cur);
+            continue;
+          }
+          cur = -1;
+        } else {
+          hub_offer(C, hub, qx, qy, qz, m, k, N, lane, (uint32_t*)(list + KC));
+        }
+      }
+    } else {
+      const int e = base + lane;
+      const bool valid = e < end;
+      float4 ps = make_float4(0.f, 0.f, 0.f, __int_as_float(0x7fffffff));
+      if (valid) ps = __ldg(C.ent + e);
+      const int s = __float_as_int(ps.w);
+      const bool inr = valid && s < m;  // rows ascend: past the first s >= m nothing is
+      const float d = sqd32(qx, qy, qz, ps);
+      const uint64_t key = pack_key(d, (uint32_t)s);
+      const bool row_done = __any_sync(0xffffffffu, valid && !inr) || base + 32 >= end;
+      if (cur >= 0) {
+        const bool cl = inr && strictly_closer_at(C, qx, qy, qz, d, ps, dcur, cur);
+        const uint32_t b = __ballot_sync(0xffffffffu, cl);
+        if (b) {
+          const int w = __ffs((int)b) - 1;
+          cur = __shfl_sync(0xffffffffu, s, w);
+          dcur = __shfl_sync(0xffffffffu, d, w);
+          const uint64_t kw = __shfl_sync(0xffffffffu, key, w);
+          if (kw < N.worst) N.insert(kw, k, lane);
+          rr = __ldg(C.rows + cur);
+          base = rr.x;
+          end = rr.y;
+          if constexpr (TREES) hub = __ldg(C.hub_of + cur);
+          continue;
+        }
+        if (row_done) cur = -1;
+      } else {
+        const bool fresh = inr && key < N.worst && !N.contains(key);
+        uint32_t b = __ballot_sync(0xffffffffu, fresh);
+        while (b) {
+          const int j = __ffs((int)b) - 1;
+          b &= b - 1;
+          const uint64_t c = __shfl_sync(0xffffffffu, key, j);
+          if (c < N.worst) N.insert(c, k, lane);
+        }
+      }
+      if (!row_done) {
+        base += 32;
         continue;
       }
-      if (row_done) cur = -1;
-    } else {
-      const bool fresh = inr && key < N.worst && !N.contains(key);
-      uint32_t b = __ballot_sync(0xffffffffu, fresh);
-      while (b) {
-        const int j = __ffs((int)b) - 1;
-        b &= b - 1;
-        const uint64_t c = __shfl_sync(0xffffffffu, key, j);
-        if (c < N.worst) N.insert(c, k, lane);
-      }
-    }
-    if (!row_done) {
-      base += 32;
-      continue;
     }
     const int pos = N.first_clear(min(N.cnt, k - 1));
     if (pos < 0) break;
@@ -1003,6 +1206,7 @@ __device__ __forceinline__ void knn_query_warp(const CloudDev& C, float qx, floa
     rr = __ldg(C.rows + site);
     base = rr.x;
     end = rr.y;
+    if constexpr (TREES) hub = __ldg(C.hub_of + site);
   }
   int32_t* oi = out_idx + (int64_t)row * k;
   float* od = out_d2 + (int64_t)row * k;

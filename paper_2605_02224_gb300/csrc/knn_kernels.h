@@ -12,6 +12,11 @@ struct CloudDevHost {
   int32_t n;
   float lo[3], hi[3];    // bounding box of the sites (query sort)
   const void* ent;       // float4[E]: succ[e]'s (x, y, z) and its rank's bits in w
+  // box trees over the long lists (hub_index.h), all NULL when there are none
+  const int32_t* hub_of = nullptr;  // [n]: the tree of site i's list, or -1
+  const void* hub_desc = nullptr;   // int4 per tree
+  const void* hub_ent = nullptr;    // float4 per entry, chunks of 32
+  const void* hub_node = nullptr;   // two float4 per node
 };
 
 // Same-manifold queries: q[i] = pts[sites[i]] and m_out[i] = the query's

@@ -215,12 +215,12 @@ cudaError_t run_smem(const CloudDevHost& c, const PlainLaunch& L, cudaStream_t s
 // One warp per query, the candidate list in shared memory (KC keys per
 // warp: 8 KB per 256-thread block at KC = 128). One block per 8 queries of
 // the processing order, started by the hardware wherever a block ends.
-template <int KC>
+template <int KC, bool TREES>
 __global__ void __launch_bounds__(kThreads) knn_plain_warp_kernel(
     CloudDev C, const float* __restrict__ q, int q_stride, int64_t nq, int k,
     const int32_t* __restrict__ mq, int m_scalar, const int32_t* __restrict__ perm,
     int32_t* __restrict__ out_idx, float* __restrict__ out_d2, int32_t* __restrict__ err) {
-  __shared__ uint64_t lists[kThreads / 32][KC];
+  __shared__ uint64_t lists[kThreads / 32][kWarpListWords(KC)];
   const int warp = (int)(threadIdx.x >> 5), lane = (int)(threadIdx.x & 31u);
   const int64_t nw = (int64_t)gridDim.x * (kThreads / 32);
   for (int64_t i = (int64_t)blockIdx.x * (kThreads / 32) + warp; i < nq; i += nw) {
@@ -236,11 +236,11 @@ __global__ void __launch_bounds__(kThreads) knn_plain_warp_kernel(
       if (lane == 0) atomicOr(err, 1);
       continue;
     }
-    knn_query_warp<KC>(C, qx, qy, qz, k, m, lists[warp], out_idx, out_d2, (int32_t)qi);
+    knn_query_warp<KC, TREES>(C, qx, qy, qz, k, m, lists[warp], out_idx, out_d2, (int32_t)qi);
   }
 }
 
-template <int KC>
+template <int KC, bool TREES>
 cudaError_t run_warp(const CloudDevHost& c, const PlainLaunch& L, cudaStream_t stream) {
   constexpr int kWarps = kThreads / 32;
   int64_t blocks = (L.nq + kWarps - 1) / kWarps;
@@ -250,7 +250,7 @@ cudaError_t run_warp(const CloudDevHost& c, const PlainLaunch& L, cudaStream_t s
     const cudaError_t oe = occ_of.with(current_device(), cudaErrorInvalidDevice, [&](int& o) {
       if (o < 1) {
         cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &o, knn_plain_warp_kernel<KC>, kThreads, 0);
+            &o, knn_plain_warp_kernel<KC, TREES>, kThreads, 0);
         if (e != cudaSuccess) {
           o = 0;
           return e;
@@ -264,8 +264,10 @@ cudaError_t run_warp(const CloudDevHost& c, const PlainLaunch& L, cudaStream_t s
     blocks = std::min<int64_t>(blocks, (int64_t)num_sms() * std::min(L.blocks_per_sm, occ));
   }
   if (blocks < 1) blocks = 1;
-  CloudDev C{(const float4*)c.pts, c.rows, c.succ, c.n, (const float4*)c.ent};
-  knn_plain_warp_kernel<KC><<<(unsigned)blocks, kThreads, 0, stream>>>(
+  CloudDev C{(const float4*)c.pts, c.rows, c.succ, c.n, (const float4*)c.ent,
+             c.hub_of,          (const int4*)c.hub_desc, (const float4*)c.hub_ent,
+             (const float4*)c.hub_node};
+  knn_plain_warp_kernel<KC, TREES><<<(unsigned)blocks, kThreads, 0, stream>>>(
       C, L.q, L.q_stride, L.nq, L.k, L.m, L.m_scalar, L.perm, L.out_idx, L.out_d2, L.err);
   return cudaGetLastError();
 }
@@ -342,9 +344,14 @@ cudaError_t pick_s(const CloudDevHost& c, const PlainLaunch& L, cudaStream_t str
 template <bool COUNT>
 cudaError_t pick_g(const CloudDevHost& c, const PlainLaunch& L, cudaStream_t stream) {
   if (!COUNT && L.lanes == 32 && L.placement == 2) {
-    if (L.k <= 32) return run_warp<32>(c, L, stream);
-    if (L.k <= 64) return run_warp<64>(c, L, stream);
-    return run_warp<128>(c, L, stream);
+    if (c.hub_of) {  // the cloud has box trees over its long lists
+      if (L.k <= 32) return run_warp<32, true>(c, L, stream);
+      if (L.k <= 64) return run_warp<64, true>(c, L, stream);
+      return run_warp<128, true>(c, L, stream);
+    }
+    if (L.k <= 32) return run_warp<32, false>(c, L, stream);
+    if (L.k <= 64) return run_warp<64, false>(c, L, stream);
+    return run_warp<128, false>(c, L, stream);
   }
   switch (L.lanes) {
     case 1: return pick_thread<COUNT>(c, L, stream);

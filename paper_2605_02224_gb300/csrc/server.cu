@@ -259,16 +259,13 @@ void mknn_server::launch(Slot& sl, std::vector<uint64_t>& tickets, size_t off, s
     int64_t pack_nq = 0;  // the pack runs as one launch per variant: its size sets the lanes
     for (int i = 0; i < nreq; ++i) pack_nq += recs[tickets[i] - 1].r.nq;
     std::vector<int> lanes(nreq), placement(nreq);
-    int64_t warp_rounds = 0;
     for (int i = 0; i < nreq; ++i) {
       const mknn_request& q = recs[tickets[i] - 1].r;
       const mknn_cloud* c = clouds[q.cloud];
       const Mode chosen = choose_mode(q.k, c->n, c->hub_bucket(), pack_nq);
       lanes[i] = o.lanes ? o.lanes : chosen.lanes;
       placement[i] = o.lanes ? default_placement(q.k, lanes[i]) : chosen.placement;
-      warp_rounds += (q.nq * lanes[i] + 31) / 32;
     }
-    const int rounds = auto_item_rounds(warp_rounds);
     for (int i = 0; i < nreq; ++i) {
       ReqRec& R = recs[tickets[i] - 1];
       const mknn_request& q = R.r;
@@ -286,9 +283,11 @@ void mknn_server::launch(Slot& sl, std::vector<uint64_t>& tickets, size_t off, s
                      (const float*)(dbase + R.q_off), nullptr,
                      sorted ? (const int32_t*)(dbase + R.perm_off) : nullptr,
                      (int32_t*)(dbase + R.idx_off), (float*)(dbase + R.d2_off), c->d_err, q.k,
-                     q.m ? q.m : (int32_t)c->n, (const float4*)cd.ent};
-      const int v = variant_index(lanes[i], q.k, placement[i]);
-      const int per = item_queries(lanes[i], plan_item_rounds(lanes[i], rounds));
+                     q.m ? q.m : (int32_t)c->n, (const float4*)cd.ent, cd.hub_of,
+                     (const int4*)cd.hub_desc, (const float4*)cd.hub_ent,
+                     (const float4*)cd.hub_node};
+      const int v = with_trees(variant_index(lanes[i], q.k, placement[i]), cd.hub_of != nullptr);
+      const int per = item_queries(lanes[i], kItemRounds);
       req_k[i] = q.k;
       for (int64_t b0 = 0; b0 < q.nq; b0 += per)
         items.push_back(Item{i, (int32_t)b0, (int32_t)std::min<int64_t>(q.nq, b0 + per), v});

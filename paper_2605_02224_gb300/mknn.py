@@ -111,6 +111,7 @@ def _declare(L):
         "mknn_cloud_free": (i32, [vp]),
         "mknn_cloud_info": (i32, [vp, vp, vp, vp]),
         "mknn_cloud_order": (i32, [vp, vp]),
+        "mknn_cloud_trees": (i32, [vp, vp, vp]),
         "mknn_cloud_table": (i32, [vp, vp, vp, vp]),
         "mknn_cloud_stats": (i32, [vp, vp]),
         "mknn_cloud_tets": (i32, [vp, vp, vp]),
@@ -247,6 +248,12 @@ def mknn_cloud_info(cloud: int):
     n, E, b = C.c_int64(), C.c_int64(), C.c_size_t()
     _check(lib().mknn_cloud_info(cloud, C.byref(n), C.byref(E), C.byref(b)))
     return n.value, E.value, b.value
+
+
+def mknn_cloud_trees(cloud: int):
+    t, e = C.c_int64(), C.c_int64()
+    _check(lib().mknn_cloud_trees(cloud, C.byref(t), C.byref(e)))
+    return t.value, e.value
 
 
 def mknn_cloud_order(cloud: int) -> np.ndarray:

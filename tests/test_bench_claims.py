@@ -47,9 +47,10 @@ def test_query_kernel_name_matches_the_dispatch():
     hdr = _read("knn_kernels.h")
     assert f"constexpr int kWarpMinK = {bench.WARP_MIN_K};" in hdr
     assert "int default_lanes(int k) { return k >= kWarpMinK ? 32 : 1; }" in _read("knn_plain.cu")
-    assert bench._query_kernel_name(0, 100, 0) == "knn_plain_warp_kernel<128>"
-    assert bench._query_kernel_name(0, 48, 0) == "knn_plain_warp_kernel<64>"
-    assert bench._query_kernel_name(32, 16, 2) == "knn_plain_warp_kernel<32>"
+    assert bench._query_kernel_name(0, 100, 0) == "knn_plain_warp_kernel<128, false>"
+    assert bench._query_kernel_name(0, 48, 0) == "knn_plain_warp_kernel<64, false>"
+    assert bench._query_kernel_name(32, 16, 2) == "knn_plain_warp_kernel<32, false>"
+    assert bench._query_kernel_name(32, 16, 2, True) == "knn_plain_warp_kernel<32, true>"
     assert bench._query_kernel_name(0, 47, 0) == "knn_plain_smem_kernel<128, 2, 0>"
     assert bench._query_kernel_name(1, 16, 1) == "knn_plain_thread_kernel"
     assert bench._query_kernel_name(8, 16, 0).startswith("knn_plain_kernel<8")
@@ -72,7 +73,9 @@ def test_plan_variant_table_matches_the_library():
     assert "reqs[r].nq < (o.sort > 0 ? 1 : 4096)" in src
     h = open(os.path.join(CSRC, "batch.h")).read()
     assert "constexpr int kWarpVariant32 = 16;" in h
+    assert "constexpr int kTreeVariant32 = 19;" in h and bench._TREE_VARIANT32 == 19
     assert table[16:19] == [(32, 1, 2), (32, 2, 2), (32, 4, 2)]
+    assert table[19:22] == table[16:19] and len(table) == 22
 
 
 def test_plan_launch_count():
@@ -88,6 +91,9 @@ def test_plan_launch_count():
     lanes2 = np.array([32, 32])
     reqs2 = [dict(k=32, nq=10), dict(k=32, nq=10)]
     assert bench._plan_launches(lanes2, reqs2, np.array([1, 2])) == 2
+    # one-warp lists on a cloud with box trees and on one without: two kernels
+    assert bench._plan_launches(lanes2, reqs2, np.array([2, 2]), [True, False]) == 2
+    assert bench._plan_launches(lanes2, reqs2, np.array([2, 2]), [True, True]) == 1
 
 
 def test_traffic_record_is_used_only_for_its_own_sources():

@@ -32,7 +32,7 @@ def _cuda():
 
 # ------------------------------------------------------------ tiny, exhaustive
 
-@pytest.mark.parametrize("n", [1, 2, 5, 17, 64, 150])
+@pytest.mark.parametrize("n", [1, 2, 5, 17, 64, 150, 4200])
 @pytest.mark.parametrize("table", ["complete", "built"])
 def test_tiny_exhaustive(n, table):
     P, _ = W.uniform_cube(n, 100 + n)
@@ -190,6 +190,72 @@ def test_hub_rows_all_variants():
                 base = (idx, d2)
             else:
                 assert np.array_equal(idx, base[0]) and np.array_equal(d2, base[1]), (k, v)
+    c.close()
+
+
+def test_box_trees_give_the_scans_rows():
+    """Successor lists of 256 entries or more get box trees, which only the
+    one-warp kernel walks (descent: the lowest-rank strictly closer entry;
+    expansion: the entries below the k-th key). The 400k-site patch cloud
+    has lists of up to ~33k entries (a tree of three levels). Queries
+    exactly on and next to the sites with the longest lists, next to those
+    lists' entries, and in the box; for every k and prefix bound the warp
+    kernel gives the same bits as the scanning kernels, sampled rows
+    against the oracle."""
+    import torch
+    n = 400_000
+    P, _ = W.patches4(n, 21200)
+    order = W.permutation(n, 21201)
+    c = built_cloud(P, order, "patches400k")
+    c.upload()
+    Pr = P[order]
+    _, rowp, succ = c.table()
+    L = np.diff(rowp)
+    assert L.max() > 32 * 1024 and (L >= 256).sum() > 100
+    trees, covered = c.trees()
+    assert trees == (L >= 256).sum() and covered == L[L >= 256].sum()
+    hubs = np.argsort(-L, kind="stable")[:64]
+    near = np.concatenate([succ[rowp[h]:rowp[h + 1]][::41] for h in hubs[:8]])[:2000]
+    Q = np.concatenate([
+        Pr[hubs],
+        Pr[hubs] + 1e-4 * W.normal(71, 1, 3 * len(hubs)).reshape(-1, 3),
+        Pr[near] + 2e-3 * W.normal(72, 1, 3 * len(near)).reshape(-1, 3),
+        W.box_queries(1500, 73, [0.0] * 3, [1.0] * 3)]).astype(np.float32)
+    nq = len(Q)
+    m = np.clip(np.floor(np.exp(W.uniform(74, 1, nq) * np.log(n))), 1, n).astype(np.int32)
+    for k in (1, 4, 32, 100):
+        for mk in (None, m):
+            tree = run_knn(c, Q, k, mk, lanes=32, placement=2)
+            scan = run_knn(c, Q, k, mk, lanes=1, placement=2)
+            assert np.array_equal(tree[0], scan[0]) and np.array_equal(tree[1], scan[1]), k
+            if k <= 64:
+                group = run_knn(c, Q, k, mk, lanes=32, placement=1)
+                assert np.array_equal(tree[0], group[0]) and np.array_equal(tree[1], group[1])
+            parity.check_rows(Pr, Q, k, mk if mk is not None else 0, *tree,
+                              rows=range(0, nq, 37))
+    # the persistent kernel's two one-warp forms in one plan: this cloud (with
+    # trees) and a sphere (no list reaches 4096 entries: no trees)
+    S, _ = W.sphere(20000, 75)
+    so = W.permutation(20000, 76)
+    cs = built_cloud(S, so, "sphere20k")
+    cs.upload()
+    assert cs.trees() == (0, 0)
+    QS = W.box_queries(3000, 77, [-1.2] * 3, [1.2] * 3)
+    for k in (4, 48):
+        outs, reqs = [], []
+        for cl, qq in ((c, Q), (cs, QS)):
+            qt = torch.from_numpy(qq).cuda()
+            oi = torch.full((len(qq), k), -9, dtype=torch.int32, device="cuda")
+            od = torch.full((len(qq), k), -9.0, dtype=torch.float32, device="cuda")
+            reqs.append(dict(cloud=cl.handle, q=qt, nq=len(qq), q_stride=3, k=k, m=None,
+                             m_scalar=0, out_idx=oi, out_d2=od))
+            outs.append((cl, qq, oi, od))
+        M.mknn_knn_batch(reqs, torch.cuda.current_stream().cuda_stream, lanes=32, placement=2)
+        torch.cuda.synchronize()
+        for cl, qq, oi, od in outs:
+            ri, rd = run_knn(cl, qq, k, None, lanes=1, placement=2)
+            assert np.array_equal(oi.cpu().numpy(), ri) and np.array_equal(od.cpu().numpy(), rd)
+    cs.close()
     c.close()
 
 
