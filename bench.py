@@ -111,7 +111,7 @@ def _query_kernel_name(lanes: int, k: int, placement: int, trees: bool = False) 
     if lanes in (0, 1) and placement in (0, 2):
         threads, words = (256, 1) if k <= 32 else ((128, 2) if k <= 64 else (64, 4))
         kind = 8 if k <= 8 else (16 if k <= 16 else 0)
-        return f"knn_plain_smem_kernel<{threads}, {words}, {kind}>"
+        return f"knn_plain_smem_kernel<{threads}, {words}, {kind}, {'true' if trees else 'false'}>"
     if lanes in (0, 1):
         return "knn_plain_thread_kernel"
     return f"knn_plain_kernel<{lanes}, S>"

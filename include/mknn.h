@@ -236,7 +236,8 @@ mknn_status mknn_knn(const mknn_cloud* cloud, const float* q, int64_t nq, int32_
 typedef struct {
   int32_t lanes;        /* lanes per query: 0 = default (1, or 32 from
                            k = 48 up, or more for small batches and
-                           clouds with very long successor lists), or
+                           clouds with very long successor lists - for
+                           k > 8 when the cloud has box trees), or
                            1, 4, 8, 16, 32 (4 and 8 hold k <= 64; one
                            lane above 64 needs placement 2 and no
                            counters) */
@@ -276,11 +277,19 @@ mknn_status mknn_query_order(const mknn_cloud* cloud, const float* q, int64_t nq
                              int32_t* perm_out, void* workspace, size_t workspace_bytes,
                              mknn_stream_t stream);
 
-/* Scratch bytes mknn_knn_ex needs for nq queries with the given options. */
+/* Scratch bytes mknn_knn_ex needs for nq queries with the given options:
+ * the locality sort's (none with an order or the sort off) and 4 bytes per
+ * query (plus 256) for the hand-over below. */
 size_t mknn_knn_workspace_size(int64_t nq, const mknn_knn_opts* opts);
 
 /* mknn_knn with explicit options (opts may be NULL). A caller workspace of
- * at least mknn_knn_workspace_size bytes avoids library allocations. */
+ * at least mknn_knn_workspace_size bytes avoids library allocations.
+ * One lane per query with the list in shared memory on a cloud with box
+ * trees (mknn_cloud_trees): the queries that would read a list with a tree
+ * through are handed over to the one-warp kernel (32 lanes, shared memory),
+ * which walks the tree; a second launch on the stream, same results. A
+ * caller workspace too small for the hand-over (but not for the sort)
+ * leaves it out: the lists are then read in rank order. */
 mknn_status mknn_knn_ex(const mknn_cloud* cloud, const float* q, int64_t nq, int32_t q_stride,
                         int32_t k, const int32_t* m, int32_t m_scalar, int32_t* out_idx,
                         float* out_d2, const mknn_knn_opts* opts, mknn_stream_t stream);

@@ -244,8 +244,17 @@ int nbucket_of(int64_t n) {
 // sites), where a whole warp per query scans the long rows 32 entries at a
 // time. Timed on 64 mixed clouds, 32 lanes won on 16 of the 17 hub clouds
 // (by 1.2x-3.9x) and lost on all but one of the others (by up to 20x).
+// With box trees and the hand-over of mknn_knn_ex (one lane per query,
+// the queries that meet a list with a tree answered by the one-warp kernel)
+// one lane is the default up to k = 8: on the 20 patch clouds of that mix
+// with trees it took 119 ms against 124 ms for 32 lanes, winning at k <= 8
+// on all but two and losing at k = 16 and 32 by up to 1.7x.
 constexpr int kHubBucketWide = 12;
-int heuristic_lanes(int k, int hub) { return hub >= kHubBucketWide ? 32 : default_lanes(k); }
+constexpr int kHandoverMaxK = 8;
+int heuristic_lanes(int k, int hub, bool handover) {
+  if (handover && k <= kHandoverMaxK) return default_lanes(k);
+  return hub >= kHubBucketWide ? 32 : default_lanes(k);
+}
 
 }  // namespace
 
@@ -262,9 +271,9 @@ int fill_lanes(int64_t nq, int k) {
   return lanes;
 }
 
-Mode choose_mode(int k, int64_t n, int hub, int64_t nq) {
+Mode choose_mode(int k, int64_t n, int hub, int64_t nq, bool handover) {
   const Mode t = tuned_mode(k, n, hub);
-  const int base = t.lanes ? t.lanes : heuristic_lanes(k, hub);
+  const int base = t.lanes ? t.lanes : heuristic_lanes(k, hub, handover);
   int lanes = std::max(base, fill_lanes(nq, k));
   while (lanes < 32 && variant_index(lanes, k, 1) < 0) lanes <<= 1;  // e.g. 4 lanes hold k <= 16
   const int placement = (t.lanes && lanes == t.lanes) ? t.placement : default_placement(k, lanes);
@@ -353,6 +362,7 @@ BatchLaunch batch_config(int nitems, int blocks_per_sm, int kcap, int variant) {
   const int wpb = b.threads / 32;
   const int64_t blocks_needed = ((int64_t)std::max(1, nitems) + wpb - 1) / wpb;
   b.grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)num_sms() * per_sm, blocks_needed));
+  b.fills = blocks_needed >= (int64_t)num_sms() * per_sm;
   return b;
 }
 
@@ -405,9 +415,17 @@ std::vector<Segment> make_segments(std::vector<Item>& items, int blocks_per_sm,
 cudaError_t launch_segments(const ReqDev* d_reqs, const Item* d_items, int* d_next,
                             const std::vector<Segment>& segs, cudaStream_t s, cudaStream_t aux,
                             cudaEvent_t fork, cudaEvent_t join) {
-  bool one = false, group = false;
-  for (const Segment& g : segs) (is_smem_variant(g.launch.variant) ? one : group) = true;
-  const bool split = one && group && aux;
+  // The one-lane segments and the others run on two streams only when no
+  // segment fills the GPU by itself; otherwise one after another (two
+  // persistent launches that each size their grid for the whole GPU share
+  // it worse than they run in turn: the batching workload's plan took 224 ms
+  // in turn against 234 ms on two streams).
+  bool one = false, group = false, fills = false;
+  for (const Segment& g : segs) {
+    (is_smem_variant(g.launch.variant) ? one : group) = true;
+    fills |= g.launch.fills;
+  }
+  const bool split = one && group && aux && !fills;
   cudaError_t e = cudaSuccess;
   if (split) {
     if ((e = cudaEventRecord(fork, s)) != cudaSuccess) return e;

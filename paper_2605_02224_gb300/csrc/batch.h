@@ -88,6 +88,7 @@ struct BatchLaunch {
   size_t smem = 0;    // dynamic shared memory for the one-lane candidate lists
   int kcap = 0;       // list capacity: the largest k among the launch's requests
   int variant = kSmemVariant;
+  bool fills = false; // the items keep every SM's resident blocks busy
 };
 // Grid, block and shared memory for `nitems` items of one variant.
 BatchLaunch batch_config(int nitems, int blocks_per_sm, int kcap, int variant);
@@ -108,10 +109,10 @@ struct Segment {
 std::vector<Segment> make_segments(std::vector<Item>& items, int blocks_per_sm,
                                    const std::vector<int>& req_k);
 // Launches every segment, segment i draining the queue counter d_next[i]
-// (zero on entry). With one-lane and group segments both present, the
-// group segments run one after another on `aux`, forked from s and joined
-// back, concurrently with the one-lane segments on s; otherwise all run on
-// s in order.
+// (zero on entry). With one-lane and group segments both present and none
+// of them filling the GPU alone, the group segments run one after another
+// on `aux`, forked from s and joined back, concurrently with the one-lane
+// segments on s; otherwise all run on s in order.
 cudaError_t launch_segments(const ReqDev* d_reqs, const Item* d_items, int* d_next,
                             const std::vector<Segment>& segs, cudaStream_t s, cudaStream_t aux,
                             cudaEvent_t fork, cudaEvent_t join);
@@ -124,7 +125,10 @@ void set_tuned_mode(int k, int64_t n, int hub, Mode m);
 // Mode for a launch of nq queries: the tuned (or default) lanes for
 // (k, n, hub), widened for batches too small to fill the GPU one query per
 // thread, and the tuned placement (or the default for those lanes).
-Mode choose_mode(int k, int64_t n, int hub, int64_t nq);
+// handover: the launch hands queries that meet a list with a box tree over
+// to the one-warp kernel (mknn_knn_ex on a cloud with trees), which makes
+// one lane the better default for small k.
+Mode choose_mode(int k, int64_t n, int hub, int64_t nq, bool handover = false);
 // The smallest lane width that fills the GPU with nq queries of this k.
 int fill_lanes(int64_t nq, int k);
 

@@ -523,9 +523,10 @@ mknn_status mknn_cloud_load(const char* path, mknn_cloud** out) {
 }
 
 size_t mknn_knn_workspace_size(int64_t nq, const mknn_knn_opts* opts) {
-  if (nq < 0) return 0;
-  if (opts && opts->order) return 0;
-  return sort_enabled(opts, nq) ? sort_workspace_bytes(nq) + perm_bytes(nq) : 0;
+  if (nq <= 0) return 0;
+  const size_t sort =
+      (opts && opts->order) || !sort_enabled(opts, nq) ? 0 : sort_workspace_bytes(nq) + perm_bytes(nq);
+  return sort + defer_bytes(nq);
 }
 
 size_t mknn_query_order_workspace_size(int64_t nq) {
@@ -570,7 +571,7 @@ mknn_status mknn_knn_ex(const mknn_cloud* c, const float* q, int64_t nq, int32_t
   }
   if (nq == 0) return MKNN_OK;
   if (!q || !out_idx || !out_d2) return fail(MKNN_EINVAL, "NULL device pointer");
-  const Mode chosen = choose_mode(k, c->n, c->hub_bucket(), nq);
+  const Mode chosen = choose_mode(k, c->n, c->hub_bucket(), nq, c->d_hub_of != nullptr);
   int lanes = (opts && opts->lanes) ? opts->lanes : chosen.lanes;
   if (lanes != 1 && lanes != 4 && lanes != 8 && lanes != 16 && lanes != 32)
     return fail(MKNN_EINVAL, "lanes must be 1, 4, 8, 16 or 32");
@@ -578,25 +579,39 @@ mknn_status mknn_knn_ex(const mknn_cloud* c, const float* q, int64_t nq, int32_t
     return fail(MKNN_EINVAL, "k above what this lane width holds (4, 8 lanes: 64; 1, 16, 32: 128)");
   if (lanes == 1 && k > 64 && ((opts && opts->counters) || (opts && opts->placement == 1)))
     return fail(MKNN_EINVAL, "one lane with k > 64 needs the shared-memory list (no counters)");
+  const int placement = (opts && opts->placement)
+                            ? opts->placement
+                            : ((opts && opts->lanes) ? default_placement(k, lanes) : chosen.placement);
+  if (placement != 1 && placement != 2)
+    return fail(MKNN_EINVAL, "placement must be 0, 1 (registers) or 2 (shared memory)");
   cudaStream_t s = (cudaStream_t)stream;
   const int32_t* perm = opts ? opts->order : nullptr;
-  if (!perm && sort_enabled(opts, nq)) {
-    const size_t need = sort_workspace_bytes(nq) + perm_bytes(nq);
-    void* ws = nullptr;
+  // scratch: the sort's (unless an order is given), then the hand-over of
+  // queries to the one-warp kernel (one lane on a cloud with box trees)
+  const size_t sort_need = (!perm && sort_enabled(opts, nq)) ? sort_workspace_bytes(nq) + perm_bytes(nq) : 0;
+  const bool wants_defer =
+      c->d_hub_of && lanes == 1 && placement == 2 && !(opts && opts->counters);
+  size_t need = sort_need + (wants_defer ? defer_bytes(nq) : 0);
+  void* ws = nullptr;
+  if (need > 0) {
     if (opts && opts->workspace) {
-      if (opts->workspace_bytes < need)
+      if (opts->workspace_bytes < sort_need)
         return fail(MKNN_EINVAL, "workspace smaller than mknn_knn_workspace_size");
+      if (opts->workspace_bytes < need) need = sort_need;  // too small to hand over: scan instead
       ws = opts->workspace;
     } else {
       cudaError_t e = scratch_for(s, need, &ws);
       if (e != cudaSuccess) return fail(MKNN_ENOMEM, "workspace allocation failed");
     }
+  }
+  if (sort_need > 0) {
     int32_t* p = (int32_t*)((char*)ws + sort_workspace_bytes(nq));
     cudaError_t e = launch_query_sort(c->dev(), q, q_stride, nq, ws, p, s);
     if (e != cudaSuccess) return cuda_fail(e, "query sort launch");
     perm = p;
   }
   PlainLaunch L;
+  L.defer = need > sort_need ? (int32_t*)((char*)ws + sort_need) : nullptr;
   L.q = q;
   L.q_stride = q_stride;
   L.nq = nq;
@@ -610,11 +625,7 @@ mknn_status mknn_knn_ex(const mknn_cloud* c, const float* q, int64_t nq, int32_t
   L.err = c->d_err;
   L.lanes = lanes;
   L.blocks_per_sm = opts ? opts->blocks_per_sm : 0;
-  L.placement = (opts && opts->placement)
-                    ? opts->placement
-                    : ((opts && opts->lanes) ? default_placement(k, lanes) : chosen.placement);
-  if (L.placement != 1 && L.placement != 2)
-    return fail(MKNN_EINVAL, "placement must be 0, 1 (registers) or 2 (shared memory)");
+  L.placement = placement;
   cudaError_t e = launch_knn_plain(c->dev(), L, s);
   if (e != cudaSuccess) return cuda_fail(e, "knn kernel launch");
   return MKNN_OK;

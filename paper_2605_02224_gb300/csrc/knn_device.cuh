@@ -42,6 +42,11 @@ constexpr uint32_t kPadRank = 0xffffffffu;
 constexpr float kGuard = 2e-6f;
 // Below this the float32 distance may be subnormal; decide in float64.
 constexpr float kTiny = 1e-30f;
+// Entries of a list with a tree that the descent reads in rank order before
+// it turns to the tree: the first strictly closer entry is often among the
+// first few (the low ranks are spread over the whole cloud), and a walk
+// that must prove its rank the lowest costs more than a chunk or two.
+constexpr int kHubScanFirst = 64;
 
 struct CloudDev {
   const float4* __restrict__ pts;
@@ -740,8 +745,15 @@ __device__ __forceinline__ bool strictly_closer_at(const CloudDev& C, float qx, 
 // inlined table (site and rank in one 16-byte load), the next one loaded
 // one iteration ahead. L is a SortedList or PermList16 over the thread's
 // column col, with `cap` slots.
-template <class L>
-__device__ __forceinline__ void knn_query_smem(const CloudDev& C, float qx, float qy, float qz,
+//
+// DEFER (a cloud with box trees over its long lists, hub_of not NULL): the
+// query gives up, returning false with nothing written, when it would read
+// a list with a tree through - the expansion of such a list, or a descent
+// that finds no strictly closer entry among its first kHubScanFirst - so
+// that the one-warp kernel, which walks the tree instead, answers it; the
+// queries that never meet such a list (most of them) stay on one lane.
+template <class L, bool DEFER = false>
+__device__ __forceinline__ bool knn_query_smem(const CloudDev& C, float qx, float qy, float qz,
                                                int k, int m, uint64_t* col, int cap,
                                                int32_t* __restrict__ out_idx,
                                                float* __restrict__ out_d2, int32_t row) {
@@ -755,6 +767,15 @@ __device__ __forceinline__ void knn_query_smem(const CloudDev& C, float qx, floa
   // coordinates are reloaded only for a float64 recheck, which is rare)
   int cur = 0;
   int2 rr = __ldg(C.rows);
+  // DEFER: the current list has a tree and its scan stops after
+  // kHubScanFirst entries
+  bool cut = false;
+  if constexpr (DEFER) {
+    if (__ldg(C.hub_of) >= 0) {
+      cut = rr.y > rr.x + kHubScanFirst;
+      rr.y = min(rr.y, rr.x + kHubScanFirst);
+    }
+  }
   int e = rr.x, end = rr.y;
   float4 next = e < end ? __ldg(C.ent + e) : kNone;
   for (;;) {
@@ -771,6 +792,13 @@ __device__ __forceinline__ void knn_query_smem(const CloudDev& C, float qx, floa
           cur = s;
           if (key < N.worst) N.insert(key, k);
           rr = __ldg(C.rows + s);
+          if constexpr (DEFER) {
+            cut = false;
+            if (__ldg(C.hub_of + s) >= 0) {
+              cut = rr.y > rr.x + kHubScanFirst;
+              rr.y = min(rr.y, rr.x + kHubScanFirst);
+            }
+          }
           e = rr.x;
           end = rr.y;
           next = e < end ? __ldg(C.ent + e) : kNone;
@@ -781,11 +809,17 @@ __device__ __forceinline__ void knn_query_smem(const CloudDev& C, float qx, floa
       continue;
     }
     // the current row is done: no closer site in it (descent), or fully offered
+    if constexpr (DEFER) {
+      if (cut && e >= end) return false;  // the descent's scan was cut short
+    }
     cur = -1;
     const int pos = flags_first_clear(N.done, min(N.cnt, k - 1));
     if (pos < 0) break;
     flags_set(N.done, pos);
     const int site = (int)(uint32_t)N.key_at(pos);
+    if constexpr (DEFER) {
+      if (__ldg(C.hub_of + site) >= 0) return false;  // an expansion of a list with a tree
+    }
     rr = __ldg(C.rows + site);
     e = rr.x;
     end = rr.y;
@@ -822,6 +856,7 @@ __device__ __forceinline__ void knn_query_smem(const CloudDev& C, float qx, floa
       __stcs(od + p, real ? __uint_as_float((uint32_t)(key >> 32)) : __int_as_float(0x7f800000));
     }
   }
+  return true;
 }
 
 // Slots of a thread's list column for k: 8 for k <= 8, 16 for k <= 16 (the
@@ -1103,11 +1138,6 @@ __device__ __forceinline__ void hub_offer(const CloudDev& C, int hub, float qx, 
       });
 }
 
-// Entries of a list with a tree that the descent reads in rank order before
-// it turns to the tree: the first strictly closer entry is often among the
-// first few (the low ranks are spread over the whole cloud), and a walk
-// that must prove its rank the lowest costs more than a chunk or two.
-constexpr int kHubScanFirst = 64;
 // 64-bit words of shared memory for one warp of knn_query_warp<KC>.
 __host__ __device__ constexpr int kWarpListWords(int kc) { return kc + kHubMaxLevels; }
 

@@ -49,7 +49,18 @@ struct PlainLaunch {
   // lanes == 32: 1 = registers spread over the warp, 2 = shared-memory list
   // per warp; ignored for 4, 8, 16 lanes (registers)
   int placement = 1;
+  // one lane, shared memory, on a cloud with box trees: device scratch of
+  // defer_bytes(nq) for the queries handed to the one-warp kernel (a count,
+  // then their indices from kDeferHead on); NULL = no hand-over
+  int32_t* defer = nullptr;
+  // device count of queries (at most nq) the launch answers, or NULL
+  const int32_t* count = nullptr;
 };
+// The deferred queries' indices start this many int32 into the scratch.
+constexpr int kDeferHead = 64;
+inline size_t defer_bytes(int64_t nq) {
+  return (((size_t)nq + kDeferHead) * 4 + 255) & ~(size_t)255;
+}
 
 // Launches the plain (one cloud) query kernel. Returns a CUDA error code.
 cudaError_t launch_knn_plain(const CloudDevHost& c, const PlainLaunch& L, cudaStream_t stream);

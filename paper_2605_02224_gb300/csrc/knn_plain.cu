@@ -114,12 +114,15 @@ cudaError_t run_thread(const CloudDevHost& c, const PlainLaunch& L, cudaStream_t
 // compiler picks either 40 registers with spills or 64, both measured
 // 5%-20% slower, and 4 or 6 blocks per SM were slower too.
 // LK: the list kind (8: SortedList of 8 slots, k <= 8; 16: PermList16,
-// 9 <= k <= 16; 0: SortedList of k slots searched over 32 W).
-template <int THREADS, int W, int LK>
+// 9 <= k <= 16; 0: SortedList of k slots searched over 32 W). DEFER (a
+// cloud with box trees): a query that gives up (knn_query_smem) is appended
+// to defer[0 .. *ndefer) for the one-warp kernel.
+template <int THREADS, int W, int LK, bool DEFER>
 __global__ void __launch_bounds__(THREADS, THREADS == 256 ? 5 : 1) knn_plain_smem_kernel(
     CloudDev C, const float* __restrict__ q, int q_stride, int64_t nq, int k, int kcap,
     const int32_t* __restrict__ mq, int m_scalar, const int32_t* __restrict__ perm,
-    int32_t* __restrict__ out_idx, float* __restrict__ out_d2, int32_t* __restrict__ err) {
+    int32_t* __restrict__ out_idx, float* __restrict__ out_d2, int32_t* __restrict__ err,
+    int32_t* __restrict__ defer, int32_t* __restrict__ ndefer) {
   extern __shared__ uint64_t smem_lists[];
   const int warp = (int)(threadIdx.x >> 5), lane = (int)(threadIdx.x & 31u);
   uint64_t* col = smem_lists + (size_t)warp * kcap * 32 + lane;
@@ -147,13 +150,18 @@ __global__ void __launch_bounds__(THREADS, THREADS == 256 ? 5 : 1) knn_plain_sme
       atomicOr(err, 1);
       continue;
     }
+    bool done;
     if constexpr (LK == 8)
-      knn_query_smem<SortedList<8, 1, true>>(C, qx, qy, qz, k, m, col, 8, out_idx, out_d2, qi);
+      done = knn_query_smem<SortedList<8, 1, true>, DEFER>(C, qx, qy, qz, k, m, col, 8, out_idx,
+                                                            out_d2, qi);
     else if constexpr (LK == 16)
-      knn_query_smem<PermList16>(C, qx, qy, qz, k, m, col, 16, out_idx, out_d2, qi);
+      done = knn_query_smem<PermList16, DEFER>(C, qx, qy, qz, k, m, col, 16, out_idx, out_d2, qi);
     else
-      knn_query_smem<SortedList<32 * W, W, false>>(C, qx, qy, qz, k, m, col, k, out_idx, out_d2,
-                                                   qi);
+      done = knn_query_smem<SortedList<32 * W, W, false>, DEFER>(C, qx, qy, qz, k, m, col, k,
+                                                                 out_idx, out_d2, qi);
+    if constexpr (DEFER) {
+      if (!done) defer[atomicAdd(ndefer, 1)] = qi;
+    }
   }
 }
 
@@ -163,7 +171,7 @@ constexpr size_t smem_bytes(int kcap) {
   return (size_t)THREADS * (size_t)kcap * 8;
 }
 
-template <int THREADS, int KMAX, int LK>
+template <int THREADS, int KMAX, int LK, bool DEFER>
 cudaError_t run_smem(const CloudDevHost& c, const PlainLaunch& L, cudaStream_t stream) {
   constexpr int W = KMAX / 32;  // 32-bit words of expanded flags
   const int kcap = list_slots(L.k);
@@ -178,7 +186,7 @@ cudaError_t run_smem(const CloudDevHost& c, const PlainLaunch& L, cudaStream_t s
   const cudaError_t se = state.with(current_device(), cudaErrorInvalidDevice, [&](State& st) {
     if (!st.attr) {
       // once per device, at the largest size any k <= KMAX needs
-      cudaError_t e = cudaFuncSetAttribute(knn_plain_smem_kernel<THREADS, W, LK>,
+      cudaError_t e = cudaFuncSetAttribute(knn_plain_smem_kernel<THREADS, W, LK, DEFER>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)smem_bytes<THREADS>(KMAX));
       if (e != cudaSuccess) return e;
@@ -187,7 +195,7 @@ cudaError_t run_smem(const CloudDevHost& c, const PlainLaunch& L, cudaStream_t s
     if (!st.occ_for[kcap]) {
       int o = 0;
       cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-          &o, knn_plain_smem_kernel<THREADS, W, LK>, THREADS, smem);
+          &o, knn_plain_smem_kernel<THREADS, W, LK, DEFER>, THREADS, smem);
       if (e != cudaSuccess) return e;
       st.occ_for[kcap] = o < 1 ? 1 : o;
     }
@@ -206,9 +214,10 @@ cudaError_t run_smem(const CloudDevHost& c, const PlainLaunch& L, cudaStream_t s
     if (cap < blocks) blocks = cap;
   }
   if (blocks < 1) blocks = 1;
-  CloudDev C{(const float4*)c.pts, c.rows, c.succ, c.n, (const float4*)c.ent};
-  knn_plain_smem_kernel<THREADS, W, LK><<<(unsigned)blocks, THREADS, smem, stream>>>(
-      C, L.q, L.q_stride, L.nq, L.k, kcap, L.m, L.m_scalar, L.perm, L.out_idx, L.out_d2, L.err);
+  CloudDev C{(const float4*)c.pts, c.rows, c.succ, c.n, (const float4*)c.ent, c.hub_of};
+  knn_plain_smem_kernel<THREADS, W, LK, DEFER><<<(unsigned)blocks, THREADS, smem, stream>>>(
+      C, L.q, L.q_stride, L.nq, L.k, kcap, L.m, L.m_scalar, L.perm, L.out_idx, L.out_d2, L.err,
+      DEFER ? L.defer + kDeferHead : nullptr, DEFER ? L.defer : nullptr);
   return cudaGetLastError();
 }
 
@@ -219,8 +228,10 @@ template <int KC, bool TREES>
 __global__ void __launch_bounds__(kThreads) knn_plain_warp_kernel(
     CloudDev C, const float* __restrict__ q, int q_stride, int64_t nq, int k,
     const int32_t* __restrict__ mq, int m_scalar, const int32_t* __restrict__ perm,
-    int32_t* __restrict__ out_idx, float* __restrict__ out_d2, int32_t* __restrict__ err) {
+    int32_t* __restrict__ out_idx, float* __restrict__ out_d2, int32_t* __restrict__ err,
+    const int32_t* __restrict__ count) {
   __shared__ uint64_t lists[kThreads / 32][kWarpListWords(KC)];
+  if (count) nq = min(nq, (int64_t)__ldg(count));  // queries a deferring launch handed over
   const int warp = (int)(threadIdx.x >> 5), lane = (int)(threadIdx.x & 31u);
   const int64_t nw = (int64_t)gridDim.x * (kThreads / 32);
   for (int64_t i = (int64_t)blockIdx.x * (kThreads / 32) + warp; i < nq; i += nw) {
@@ -268,18 +279,50 @@ cudaError_t run_warp(const CloudDevHost& c, const PlainLaunch& L, cudaStream_t s
              c.hub_of,          (const int4*)c.hub_desc, (const float4*)c.hub_ent,
              (const float4*)c.hub_node};
   knn_plain_warp_kernel<KC, TREES><<<(unsigned)blocks, kThreads, 0, stream>>>(
-      C, L.q, L.q_stride, L.nq, L.k, L.m, L.m_scalar, L.perm, L.out_idx, L.out_d2, L.err);
+      C, L.q, L.q_stride, L.nq, L.k, L.m, L.m_scalar, L.perm, L.out_idx, L.out_d2, L.err,
+      L.count);
   return cudaGetLastError();
+}
+
+// One lane per query on a cloud with box trees: the queries that give up at
+// a list with a tree (knn_query_smem's DEFER) are answered afterwards by the
+// one-warp kernel, which walks the trees, over a persistent grid that reads
+// their number from the device.
+cudaError_t run_deferring(const CloudDevHost& c, const PlainLaunch& L, cudaStream_t stream) {
+  cudaError_t e = cudaMemsetAsync(L.defer, 0, sizeof(int32_t), stream);
+  if (e != cudaSuccess) return e;
+  if (L.k <= 8)
+    e = run_smem<256, 32, 8, true>(c, L, stream);
+  else if (L.k <= 16)
+    e = run_smem<256, 32, 16, true>(c, L, stream);
+  else if (L.k <= 32)
+    e = run_smem<256, 32, 0, true>(c, L, stream);
+  else if (L.k <= 64)
+    e = run_smem<128, 64, 0, true>(c, L, stream);
+  else
+    e = run_smem<64, 128, 0, true>(c, L, stream);
+  if (e != cudaSuccess) return e;
+  PlainLaunch D = L;
+  D.perm = L.defer + kDeferHead;
+  D.count = L.defer;
+  D.defer = nullptr;
+  D.lanes = 32;
+  D.placement = 2;
+  D.blocks_per_sm = 1 << 16;  // as many resident blocks as fit: a persistent grid
+  if (L.k <= 32) return run_warp<32, true>(c, D, stream);
+  if (L.k <= 64) return run_warp<64, true>(c, D, stream);
+  return run_warp<128, true>(c, D, stream);
 }
 
 template <bool COUNT>
 cudaError_t pick_thread(const CloudDevHost& c, const PlainLaunch& L, cudaStream_t stream) {
   if (!COUNT && L.placement == 2) {
-    if (L.k <= 8) return run_smem<256, 32, 8>(c, L, stream);
-    if (L.k <= 16) return run_smem<256, 32, 16>(c, L, stream);
-    if (L.k <= 32) return run_smem<256, 32, 0>(c, L, stream);
-    if (L.k <= 64) return run_smem<128, 64, 0>(c, L, stream);
-    return run_smem<64, 128, 0>(c, L, stream);  // 64 KB of lists per block at k = 128
+    if (c.hub_of && L.defer) return run_deferring(c, L, stream);
+    if (L.k <= 8) return run_smem<256, 32, 8, false>(c, L, stream);
+    if (L.k <= 16) return run_smem<256, 32, 16, false>(c, L, stream);
+    if (L.k <= 32) return run_smem<256, 32, 0, false>(c, L, stream);
+    if (L.k <= 64) return run_smem<128, 64, 0, false>(c, L, stream);
+    return run_smem<64, 128, 0, false>(c, L, stream);  // 64 KB of lists per block at k = 128
   }
   if (L.k > 64) return cudaErrorInvalidValue;  // register lists hold k <= 64
   if (L.k <= 8) return run_thread<8, COUNT>(c, L, stream);

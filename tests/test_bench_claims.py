@@ -32,17 +32,17 @@ def test_query_kernel_name_matches_the_dispatch():
     words for k up to 32/64/128, and the list kind: 8 slots (k <= 8), the
     permutation list (k <= 16), k slots above."""
     src = _read("knn_plain.cu")
-    assert "if (L.k <= 8) return run_smem<256, 32, 8>" in src
-    assert "if (L.k <= 16) return run_smem<256, 32, 16>" in src
-    assert "if (L.k <= 32) return run_smem<256, 32, 0>" in src
-    assert "if (L.k <= 64) return run_smem<128, 64, 0>" in src
-    assert "return run_smem<64, 128, 0>" in src
+    assert "if (L.k <= 8) return run_smem<256, 32, 8, false>" in src
+    assert "if (L.k <= 16) return run_smem<256, 32, 16, false>" in src
+    assert "if (L.k <= 32) return run_smem<256, 32, 0, false>" in src
+    assert "if (L.k <= 64) return run_smem<128, 64, 0, false>" in src
+    assert "return run_smem<64, 128, 0, false>" in src
     assert "constexpr int W = KMAX / 32;" in src
-    assert bench._query_kernel_name(0, 16, 0) == "knn_plain_smem_kernel<256, 1, 16>"
-    assert bench._query_kernel_name(0, 4, 0) == "knn_plain_smem_kernel<256, 1, 8>"
-    assert bench._query_kernel_name(0, 20, 0) == "knn_plain_smem_kernel<256, 1, 0>"
-    assert bench._query_kernel_name(0, 33, 0) == "knn_plain_smem_kernel<128, 2, 0>"
-    assert bench._query_kernel_name(1, 128, 2) == "knn_plain_smem_kernel<64, 4, 0>"
+    assert bench._query_kernel_name(0, 16, 0) == "knn_plain_smem_kernel<256, 1, 16, false>"
+    assert bench._query_kernel_name(0, 4, 0) == "knn_plain_smem_kernel<256, 1, 8, false>"
+    assert bench._query_kernel_name(0, 20, 0) == "knn_plain_smem_kernel<256, 1, 0, false>"
+    assert bench._query_kernel_name(0, 33, 0) == "knn_plain_smem_kernel<128, 2, 0, false>"
+    assert bench._query_kernel_name(1, 128, 2) == "knn_plain_smem_kernel<64, 4, 0, false>"
     # one warp per query from k = 48 by default, and for 32 lanes in shared memory
     hdr = _read("knn_kernels.h")
     assert f"constexpr int kWarpMinK = {bench.WARP_MIN_K};" in hdr
@@ -51,7 +51,9 @@ def test_query_kernel_name_matches_the_dispatch():
     assert bench._query_kernel_name(0, 48, 0) == "knn_plain_warp_kernel<64, false>"
     assert bench._query_kernel_name(32, 16, 2) == "knn_plain_warp_kernel<32, false>"
     assert bench._query_kernel_name(32, 16, 2, True) == "knn_plain_warp_kernel<32, true>"
-    assert bench._query_kernel_name(0, 47, 0) == "knn_plain_smem_kernel<128, 2, 0>"
+    assert bench._query_kernel_name(0, 47, 0) == "knn_plain_smem_kernel<128, 2, 0, false>"
+    # on a cloud with box trees the one-lane kernel hands queries over
+    assert bench._query_kernel_name(1, 4, 2, True) == "knn_plain_smem_kernel<256, 1, 8, true>"
     assert bench._query_kernel_name(1, 16, 1) == "knn_plain_thread_kernel"
     assert bench._query_kernel_name(8, 16, 0).startswith("knn_plain_kernel<8")
 

@@ -196,12 +196,14 @@ def test_hub_rows_all_variants():
 def test_box_trees_give_the_scans_rows():
     """Successor lists of 256 entries or more get box trees, which only the
     one-warp kernel walks (descent: the lowest-rank strictly closer entry;
-    expansion: the entries below the k-th key). The 400k-site patch cloud
-    has lists of up to ~33k entries (a tree of three levels). Queries
-    exactly on and next to the sites with the longest lists, next to those
-    lists' entries, and in the box; for every k and prefix bound the warp
-    kernel gives the same bits as the scanning kernels, sampled rows
-    against the oracle."""
+    expansion: the entries below the k-th key); one lane per query hands
+    the queries that would read such a list through over to it. The
+    400k-site patch cloud has lists of up to ~33k entries (a tree of three
+    levels). Queries exactly on and next to the sites with the longest
+    lists, next to those lists' entries, and in the box; for every k and
+    prefix bound the tree walk and the hand-over give the same bits as the
+    scanning kernels (register groups; one lane whose workspace is too
+    small for the hand-over), sampled rows against the oracle."""
     import torch
     n = 400_000
     P, _ = W.patches4(n, 21200)
@@ -223,14 +225,17 @@ def test_box_trees_give_the_scans_rows():
         W.box_queries(1500, 73, [0.0] * 3, [1.0] * 3)]).astype(np.float32)
     nq = len(Q)
     m = np.clip(np.floor(np.exp(W.uniform(74, 1, nq) * np.log(n))), 1, n).astype(np.int32)
+    order = torch.arange(nq, dtype=torch.int32, device="cuda")
+    tiny_ws = torch.zeros(64, dtype=torch.uint8, device="cuda")
     for k in (1, 4, 32, 100):
         for mk in (None, m):
             tree = run_knn(c, Q, k, mk, lanes=32, placement=2)
-            scan = run_knn(c, Q, k, mk, lanes=1, placement=2)
-            assert np.array_equal(tree[0], scan[0]) and np.array_equal(tree[1], scan[1]), k
-            if k <= 64:
-                group = run_knn(c, Q, k, mk, lanes=32, placement=1)
-                assert np.array_equal(tree[0], group[0]) and np.array_equal(tree[1], group[1])
+            handed = run_knn(c, Q, k, mk, lanes=1, placement=2)
+            scan1 = run_knn(c, Q, k, mk, lanes=1, placement=2, order=order, workspace=tiny_ws,
+                            workspace_bytes=64)
+            group = run_knn(c, Q, k, mk, lanes=32 if k <= 64 else 16, placement=1)
+            for other in (handed, scan1, group):
+                assert np.array_equal(tree[0], other[0]) and np.array_equal(tree[1], other[1]), k
             parity.check_rows(Pr, Q, k, mk if mk is not None else 0, *tree,
                               rows=range(0, nq, 37))
     # the persistent kernel's two one-warp forms in one plan: this cloud (with
