@@ -362,7 +362,6 @@ BatchLaunch batch_config(int nitems, int blocks_per_sm, int kcap, int variant) {
   const int wpb = b.threads / 32;
   const int64_t blocks_needed = ((int64_t)std::max(1, nitems) + wpb - 1) / wpb;
   b.grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)num_sms() * per_sm, blocks_needed));
-  b.fills = blocks_needed >= (int64_t)num_sms() * per_sm;
   return b;
 }
 
@@ -414,18 +413,10 @@ std::vector<Segment> make_segments(std::vector<Item>& items, int blocks_per_sm,
 
 cudaError_t launch_segments(const ReqDev* d_reqs, const Item* d_items, int* d_next,
                             const std::vector<Segment>& segs, cudaStream_t s, cudaStream_t aux,
-                            cudaEvent_t fork, cudaEvent_t join) {
-  // The one-lane segments and the others run on two streams only when no
-  // segment fills the GPU by itself; otherwise one after another (two
-  // persistent launches that each size their grid for the whole GPU share
-  // it worse than they run in turn: the batching workload's plan took 224 ms
-  // in turn against 234 ms on two streams).
-  bool one = false, group = false, fills = false;
-  for (const Segment& g : segs) {
-    (is_smem_variant(g.launch.variant) ? one : group) = true;
-    fills |= g.launch.fills;
-  }
-  const bool split = one && group && aux && !fills;
+                            cudaEvent_t fork, cudaEvent_t join, int64_t queries) {
+  bool one = false, group = false;
+  for (const Segment& g : segs) (is_smem_variant(g.launch.variant) ? one : group) = true;
+  const bool split = one && group && aux && queries <= kSplitMaxQueries;
   cudaError_t e = cudaSuccess;
   if (split) {
     if ((e = cudaEventRecord(fork, s)) != cudaSuccess) return e;
@@ -516,7 +507,7 @@ cudaError_t enqueue(mknn_batch* b, cudaStream_t s) {
     if (e != cudaSuccess) return e;
   }
   return launch_segments(b->d_reqs, b->d_items, b->d_next, b->segs, s, b->aux, b->ev_fork,
-                         b->ev_join);
+                         b->ev_join, b->total_queries);
 }
 
 }  // namespace

@@ -88,7 +88,6 @@ struct BatchLaunch {
   size_t smem = 0;    // dynamic shared memory for the one-lane candidate lists
   int kcap = 0;       // list capacity: the largest k among the launch's requests
   int variant = kSmemVariant;
-  bool fills = false; // the items keep every SM's resident blocks busy
 };
 // Grid, block and shared memory for `nitems` items of one variant.
 BatchLaunch batch_config(int nitems, int blocks_per_sm, int kcap, int variant);
@@ -109,13 +108,20 @@ struct Segment {
 std::vector<Segment> make_segments(std::vector<Item>& items, int blocks_per_sm,
                                    const std::vector<int>& req_k);
 // Launches every segment, segment i draining the queue counter d_next[i]
-// (zero on entry). With one-lane and group segments both present and none
-// of them filling the GPU alone, the group segments run one after another
-// on `aux`, forked from s and joined back, concurrently with the one-lane
-// segments on s; otherwise all run on s in order.
+// (zero on entry). With one-lane and group segments both present in a
+// launch of at most kSplitMaxQueries queries, the group segments run one
+// after another on `aux`, forked from s and joined back, concurrently with
+// the one-lane segments on s; otherwise all run on s in order. Two
+// persistent launches that each size their grid for the whole GPU fill
+// each other's tails in a small launch, and share the GPU worse than they
+// run in turn in a large one: the 64-cloud batching plan (57.6M queries)
+// took 224 ms in turn against 234 ms on two streams, while the serving
+// loop (packs of at most 2^17 queries) saturated at 6,510 requests/s on
+// two streams against 5,717 in turn.
+constexpr int64_t kSplitMaxQueries = int64_t(1) << 21;
 cudaError_t launch_segments(const ReqDev* d_reqs, const Item* d_items, int* d_next,
                             const std::vector<Segment>& segs, cudaStream_t s, cudaStream_t aux,
-                            cudaEvent_t fork, cudaEvent_t join);
+                            cudaEvent_t fork, cudaEvent_t join, int64_t queries);
 
 // Mode recorded by the tuner for (k, n, hub), lanes 0 if none. The tuning
 // table is keyed by k, floor(log2 n) and the cloud's hub bucket

@@ -315,7 +315,7 @@ void mknn_server::launch(Slot& sl, std::vector<uint64_t>& tickets, size_t off, s
     // second stream, joined before the copies back
     if (e == cudaSuccess)
       e = launch_segments((const ReqDev*)(dbase + reqs_off), (const Item*)(dbase + items_off),
-                          d_next, segs, s, sl.aux, sl.fork, sl.join);
+                          d_next, segs, s, sl.aux, sl.fork, sl.join, pack_nq);
     if (e == cudaSuccess) e = cudaEventRecord(sl.t_kern, s);
     for (int i = 0; i < nreq && e == cudaSuccess; ++i) {
       ReqRec& R = recs[tickets[i] - 1];
