@@ -618,17 +618,22 @@ def serving_section(args, M, torch, built=None):
 _PLAN_VARIANTS = [(4, 1, 1), (4, 2, 1), (4, 4, 1), (8, 1, 1), (8, 2, 1), (8, 4, 1), (8, 8, 1),
                   (16, 1, 1), (16, 2, 1), (16, 4, 1), (32, 1, 1), (32, 2, 1), (1, 64, 2),
                   (16, 8, 1), (32, 4, 1), (1, 128, 2), (32, 1, 2), (32, 2, 2), (32, 4, 2),
-                  (32, 1, 2), (32, 2, 2), (32, 4, 2)]
-# index of the first one-warp variant with box trees (the last three entries)
+                  (32, 1, 2), (32, 2, 2), (32, 4, 2), (1, 64, 2), (1, 128, 2)]
+# index of the first one-warp variant with box trees, and of the one-lane
+# variants that hand queries over to it (plans on clouds with trees)
 _TREE_VARIANT32 = 19
+_HANDOVER_VARIANT = 22
 
 
 def _plan_launches(lanes, reqs, placement=None, trees=None) -> int:
     """Kernels one plan replay launches: the locality sort's five per request
-    of at least 4096 queries, and one persistent kernel per variant present
-    (the fewest slots per lane that hold the request's k; a one-warp
-    variant has a second form for clouds with box trees, trees[i])."""
-    variants = set()
+    of at least 4096 queries, one persistent kernel per (variant, list class)
+    present (the fewest slots per lane that hold the request's k; one-lane
+    segments are cut by list class: 8, 16, 32, 64 slots; on clouds with box
+    trees, trees[i], a one-warp variant has a tree form and a one-lane
+    variant a hand-over form), and one one-warp launch per hand-over class
+    (k <= 32, <= 64, <= 128) present."""
+    segs, handover = set(), set()
     placement = placement if placement is not None else [2 if g in (1, 32) else 1 for g in lanes]
     trees = trees if trees is not None else [False] * len(reqs)
     for g, p, r, t in zip(lanes.tolist() if hasattr(lanes, "tolist") else lanes,
@@ -638,10 +643,17 @@ def _plan_launches(lanes, reqs, placement=None, trees=None) -> int:
         fits = [i for i, v in enumerate(_PLAN_VARIANTS[:_TREE_VARIANT32])
                 if v[0] == g and v[2] == lst and v[0] * v[1] >= r["k"]]
         v = min(fits, key=lambda i: _PLAN_VARIANTS[i][1])
+        cls = 0
+        if g == 1:
+            slots = 8 if r["k"] <= 8 else (16 if r["k"] <= 16 else r["k"])
+            cls = 0 if slots <= 8 else (1 if slots <= 16 else (2 if slots <= 32 else 3))
         if t and g == 32 and lst == 2:
             v += _TREE_VARIANT32 - 16
-        variants.add(v)
-    return len(variants) + 5 * sum(1 for r in reqs if r["nq"] >= 4096)
+        if t and g == 1:
+            v = _HANDOVER_VARIANT + (1 if v == 15 else 0)
+            handover.add(0 if r["k"] <= 32 else (1 if r["k"] <= 64 else 2))
+        segs.add((v, cls))
+    return len(segs) + len(handover) + 5 * sum(1 for r in reqs if r["nq"] >= 4096)
 
 
 def batch_section(args, M, torch, built=None):
@@ -1198,7 +1210,32 @@ def main():
             t0 = time.perf_counter()
             M.mknn_knn_host(cloud.handle, qh, k, None, 0, oh_i, oh_d)
             e2e_t.append(time.perf_counter() - t0)
-        return max_over_ranks(float(np.mean(e2e_t)), dist, dev), bool(torch.equal(oh_i, idx.cpu()))
+        agree = bool(torch.equal(oh_i, idx.cpu()))  # before the copies below overwrite oh_i
+        # the call's phases alone, for comparison: the same copies on one
+        # stream with nothing to overlap (CUDA events), and the device-path step
+        qd = torch.empty((nq, 3), dtype=torch.float32, device=dev)
+        od = torch.empty((nq, k), dtype=torch.float32, device=dev)
+        strm = torch.cuda.current_stream(dev)
+
+        def timed_copy(fn):
+            fn()
+            ms = []
+            for _ in range(3):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(strm)
+                fn()
+                b.record(strm)
+                torch.cuda.synchronize()
+                ms.append(a.elapsed_time(b))
+            return float(np.median(ms))
+        h2d = timed_copy(lambda: qd.copy_(qh, non_blocking=True))
+        d2h = timed_copy(lambda: (oh_i.copy_(idx, non_blocking=True),
+                                  oh_d.copy_(od, non_blocking=True)))
+        phases = {"h2d_alone_ms": h2d, "device_step_ms": float(np.mean(step_ms)),
+                  "d2h_alone_ms": d2h,
+                  "note": "the copies timed alone on one stream, and the device-path step; the "
+                          "host-buffer call overlaps them over two streams in 2^20-query chunks"}
+        return max_over_ranks(float(np.mean(e2e_t)), dist, dev), agree, phases
 
     kern_s = float(np.mean(kern_ms)) / 1e3
     khash = _kernel_hash()
@@ -1212,7 +1249,7 @@ def main():
 
     no_sort = k_sweep = prefix = batch = serving = cpu = sites = None
     if not extras:
-        e2e_s, agree = end_to_end()
+        e2e_s, agree, phases = end_to_end()
     else:
         # the same step without the locality sort (queries in input order)
         ms_ns, clk_ns = _clocked(local, lambda: _timed_ms(
@@ -1248,7 +1285,7 @@ def main():
         # copies and staging are timed, so the host cores should be free)
         for j in jobs.values():
             j.result()
-        e2e_s, agree = end_to_end()
+        e2e_s, agree, phases = end_to_end()
         P_ranked, rowp, succ = cloud.table()
         del q, idx, d2, perm, ws
         torch.cuda.empty_cache()
@@ -1281,7 +1318,8 @@ def main():
             "cpu_baseline": cpu,
             "e2e": {"value": world * nq / e2e_s, "unit": UNIT,
                     "h2d_bytes_per_step": nq * 12, "d2h_bytes_per_step": nq * k * 8,
-                    "ms_per_step": e2e_s * 1e3, "matches_device_path": agree},
+                    "ms_per_step": e2e_s * 1e3, "matches_device_path": agree,
+                    "phases": phases},
             # per step: the query kernel, and unless --no-sort the locality sort's five
             # (bounding box, histogram, two scan levels, scatter)
             "gpu_launches": (1 if args.no_sort else 6) * args.steps,

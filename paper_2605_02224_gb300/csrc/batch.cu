@@ -50,7 +50,7 @@ constexpr VariantDesc kVariants[] = {{4, 1, 1},  {4, 2, 1},  {4, 4, 1},  {8, 1, 
                                      {16, 2, 1}, {16, 4, 1}, {32, 1, 1}, {32, 2, 1},
                                      {1, 64, 2}, {16, 8, 1}, {32, 4, 1}, {1, 128, 2},
                                      {32, 1, 2}, {32, 2, 2}, {32, 4, 2}, {32, 1, 2},
-                                     {32, 2, 2}, {32, 4, 2}};
+                                     {32, 2, 2}, {32, 4, 2}, {1, 64, 2},  {1, 128, 2}};
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 static_assert(kVariants[kSmemVariant].g == 1 && kVariants[kSmemVariant128].g == 1,
               "one-lane variant indices");
@@ -58,8 +58,11 @@ static_assert(kVariants[kWarpVariant32].g == 32 && kVariants[kWarpVariant32].lis
                   kVariants[kWarpVariant32 + 2].s == 4,
               "warp variant indices");
 static_assert(kVariants[kTreeVariant32].g == 32 && kVariants[kTreeVariant32].list == 2 &&
-                  kVariants[kTreeVariant32 + 2].s == 4 && kTreeVariant32 + 3 == kNumVariants,
+                  kVariants[kTreeVariant32 + 2].s == 4 && kTreeVariant32 + 3 == kHandoverVariant,
               "tree variant indices");
+static_assert(kVariants[kHandoverVariant].g == 1 && kVariants[kHandoverVariant].s == 64 &&
+                  kVariants[kHandoverVariant128].s == 128 && kHandoverVariant128 + 1 == kNumVariants,
+              "hand-over variant indices");
 
 }  // namespace
 
@@ -78,6 +81,33 @@ int variant_index(int g, int k, int placement) {
 
 namespace {
 
+// One query by the list kind that suits its k (the thread's column holds
+// at least list_slots(k) slots). W: flag words of the kernel's k class.
+// DEFER: as knn_query_smem (false when the query was given up).
+template <int W, bool DEFER = false>
+__device__ __forceinline__ bool knn_query_smem_any(const CloudDev& C, float qx, float qy,
+                                                   float qz, int k, int m, uint64_t* col,
+                                                   int32_t* __restrict__ out_idx,
+                                                   float* __restrict__ out_d2, int32_t row) {
+  if constexpr (W == 1) {
+    if (k <= 8)
+      return knn_query_smem<SortedList<8, 1, true>, DEFER>(C, qx, qy, qz, k, m, col, 8, out_idx,
+                                                           out_d2, row);
+    else if (k <= 16)
+      return knn_query_smem<PermList16, DEFER>(C, qx, qy, qz, k, m, col, 16, out_idx, out_d2,
+                                               row);
+    else
+      return knn_query_smem<SortedList<32, 1, false>, DEFER>(C, qx, qy, qz, k, m, col, k,
+                                                             out_idx, out_d2, row);
+  } else if constexpr (W == 2) {
+    return knn_query_smem<SortedList<64, 2, false>, DEFER>(C, qx, qy, qz, k, m, col, k, out_idx,
+                                                           out_d2, row);
+  } else {
+    return knn_query_smem<SortedList<128, 4, false>, DEFER>(C, qx, qy, qz, k, m, col, k,
+                                                            out_idx, out_d2, row);
+  }
+}
+
 // This thread's column of its warp's shared-memory candidate lists.
 __device__ __forceinline__ uint64_t* smem_column(int kcap) {
   extern __shared__ uint64_t batch_lists[];
@@ -85,10 +115,12 @@ __device__ __forceinline__ uint64_t* smem_column(int kcap) {
   return batch_lists + (size_t)warp * kcap * 32 + lane;
 }
 
-template <int W>
+// DEFER: a query that meets a list with a box tree is handed over
+// (appended to the plan's list of its class) instead of answered.
+template <int W, bool DEFER>
 __device__ __forceinline__ void serve_item_smem(const ReqDev& R, const Item& w, uint64_t* col) {
   const int lane = (int)(threadIdx.x & 31u);
-  const CloudDev C{R.pts, R.rows, R.succ, R.n, R.ent};
+  const CloudDev C{R.pts, R.rows, R.succ, R.n, R.ent, DEFER ? R.hub_of : nullptr};
   for (int i = w.begin + lane; i < w.end; i += 32) {
     const int64_t qi = R.perm ? (int64_t)__ldg(R.perm + i) : (int64_t)i;
     const float* qp = R.q + qi * R.q_stride;
@@ -104,7 +136,14 @@ __device__ __forceinline__ void serve_item_smem(const ReqDev& R, const Item& w, 
       atomicOr(R.err, 1);
       continue;
     }
-    knn_query_smem_any<W>(C, qx, qy, qz, R.k, m, col, R.out_idx, R.out_d2, (int32_t)qi);
+    const bool done =
+        knn_query_smem_any<W, DEFER>(C, qx, qy, qz, R.k, m, col, R.out_idx, R.out_d2, (int32_t)qi);
+    if constexpr (DEFER) {
+      if (!done) {
+        const int c = handover_class(R.k);
+        R.ho->list[c][atomicAdd(&R.ho->count[c], 1)] = make_int2(w.req, (int)qi);
+      }
+    }
   }
 }
 
@@ -155,7 +194,7 @@ __global__ void __launch_bounds__(kThreads, S <= 2 ? 5 : (S <= 4 ? 4 : 3)) knn_b
 
 // The one-lane variant: one query per thread, candidate lists in shared
 // memory, 256-thread blocks held to 48 registers as in the plain kernel.
-template <int THREADS, int W>
+template <int THREADS, int W, bool DEFER>
 __global__ void __launch_bounds__(THREADS, THREADS == 256 ? 5 : 1) knn_batch_smem_kernel(const ReqDev* __restrict__ reqs,
                                                                  const Item* __restrict__ items,
                                                                  int nitems,
@@ -169,7 +208,7 @@ __global__ void __launch_bounds__(THREADS, THREADS == 256 ? 5 : 1) knn_batch_sme
     it = __shfl_sync(0xffffffffu, it, 0);
     if (it >= nitems) return;
     const Item w = items[it];
-    serve_item_smem<W>(reqs[w.req], w, col);
+    serve_item_smem<W, DEFER>(reqs[w.req], w, col);
     __syncwarp();
   }
 }
@@ -212,6 +251,36 @@ __global__ void __launch_bounds__(kThreads) knn_batch_warp_kernel(const ReqDev* 
       knn_query_warp<KC, TREES>(C, qx, qy, qz, R.k, m, lists[warp], R.out_idx, R.out_d2,
                                 (int32_t)qi);
     }
+    __syncwarp();
+  }
+}
+
+// The queries a plan's one-lane items handed over (class cls, one-warp
+// lists of KC keys): one warp per query, the box trees walked; launched
+// after every segment, it reads the number handed over from the device.
+template <int KC>
+__global__ void __launch_bounds__(kThreads) knn_batch_handover_kernel(
+    const ReqDev* __restrict__ reqs, Handover* __restrict__ ho, int cls) {
+  __shared__ uint64_t lists[kThreads / 32][kWarpListWords(KC)];
+  const int warp = (int)(threadIdx.x >> 5);
+  const uint32_t lane = threadIdx.x & 31u;
+  const int n = ho->count[cls];
+  const int2* __restrict__ list = ho->list[cls];
+  for (;;) {
+    int it = 0;
+    if (lane == 0) it = atomicAdd(&ho->taken[cls], 1);
+    it = __shfl_sync(0xffffffffu, it, 0);
+    if (it >= n) return;
+    const int2 pr = list[it];
+    const ReqDev& R = reqs[pr.x];
+    const CloudDev C{R.pts,    R.rows,     R.succ,    R.n,       R.ent,
+                     R.hub_of, R.hub_desc, R.hub_ent, R.hub_node};
+    const int64_t qi = pr.y;
+    const float* qp = R.q + qi * R.q_stride;
+    const float qx = __ldg(qp), qy = __ldg(qp + 1), qz = __ldg(qp + 2);
+    const int m = R.m ? __ldg(R.m + qi) : R.m_scalar;  // checked by the one-lane item
+    knn_query_warp<KC, true>(C, qx, qy, qz, R.k, m, lists[warp], R.out_idx, R.out_d2,
+                             (int32_t)qi);
     __syncwarp();
   }
 }
@@ -287,17 +356,19 @@ namespace {
 PerDevice<int> g_attr_set;
 
 cudaError_t set_smem_attributes() {
-  cudaError_t e = cudaFuncSetAttribute(knn_batch_smem_kernel<256, 1>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)list_bytes(256, 32));
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(knn_batch_smem_kernel<128, 2>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)list_bytes(128, 64));
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(knn_batch_smem_kernel<64, 4>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)list_bytes(64, 128));
+  const struct {
+    const void* fn;
+    size_t bytes;
+  } kernels[] = {{(const void*)knn_batch_smem_kernel<256, 1, false>, list_bytes(256, 32)},
+                 {(const void*)knn_batch_smem_kernel<128, 2, false>, list_bytes(128, 64)},
+                 {(const void*)knn_batch_smem_kernel<64, 4, false>, list_bytes(64, 128)},
+                 {(const void*)knn_batch_smem_kernel<256, 1, true>, list_bytes(256, 32)},
+                 {(const void*)knn_batch_smem_kernel<128, 2, true>, list_bytes(128, 64)},
+                 {(const void*)knn_batch_smem_kernel<64, 4, true>, list_bytes(64, 128)}};
+  cudaError_t e = cudaSuccess;
+  for (const auto& kn : kernels)
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(kn.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kn.bytes);
   return e;
 }
 
@@ -334,9 +405,13 @@ const void* variant_kernel(int variant, int threads) {
     case kTreeVariant32 + 1: return (const void*)knn_batch_warp_kernel<64, true>;
     case kTreeVariant32 + 2: return (const void*)knn_batch_warp_kernel<128, true>;
     case kSmemVariant:
-      return threads == 256 ? (const void*)knn_batch_smem_kernel<256, 1>
-                            : (const void*)knn_batch_smem_kernel<128, 2>;
-    case kSmemVariant128: return (const void*)knn_batch_smem_kernel<64, 4>;
+      return threads == 256 ? (const void*)knn_batch_smem_kernel<256, 1, false>
+                            : (const void*)knn_batch_smem_kernel<128, 2, false>;
+    case kSmemVariant128: return (const void*)knn_batch_smem_kernel<64, 4, false>;
+    case kHandoverVariant:
+      return threads == 256 ? (const void*)knn_batch_smem_kernel<256, 1, true>
+                            : (const void*)knn_batch_smem_kernel<128, 2, true>;
+    case kHandoverVariant128: return (const void*)knn_batch_smem_kernel<64, 4, true>;
     default: return nullptr;
   }
 }
@@ -349,7 +424,7 @@ BatchLaunch batch_config(int nitems, int blocks_per_sm, int kcap, int variant) {
   b.variant = variant;
   const bool smem = is_smem_variant(variant);
   b.kcap = smem ? kcap : 0;
-  b.threads = variant == kSmemVariant128 ? 64 : smem ? (kcap <= 32 ? 256 : 128) : kThreads;
+  b.threads = is_smem128_variant(variant) ? 64 : smem ? (kcap <= 32 ? 256 : 128) : kThreads;
   b.smem = smem ? list_bytes(b.threads, kcap) : 0;
   int occ = 1;
   const void* fn = variant_kernel(variant, b.threads);
@@ -468,6 +543,12 @@ struct mknn_batch {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   int64_t total_queries = 0;
+  // hand-over of one-lane items on clouds with box trees: the lists and
+  // counters (device), and which classes a run must drain
+  Handover* d_ho = nullptr;
+  int2* d_ho_pairs = nullptr;
+  bool ho_class[3] = {false, false, false};
+  int ho_grid[3] = {0, 0, 0};
 };
 
 namespace {
@@ -485,17 +566,48 @@ void free_plan(mknn_batch* b) {
   cudaFree(b->d_items);
   cudaFree(b->d_next);
   cudaFree(b->d_ws);
+  cudaFree(b->d_ho);
+  cudaFree(b->d_ho_pairs);
   if (b->ev_fork) cudaEventDestroy(b->ev_fork);
   if (b->ev_join) cudaEventDestroy(b->ev_join);
   if (b->aux) cudaStreamDestroy(b->aux);
   delete b;
 }
 
-// Enqueues the plan's work on stream s: the locality sorts, then the
-// persistent launch of each segment.
+// The one-warp kernel of hand-over class c and its persistent grid.
+const void* handover_kernel(int c) {
+  return c == 0 ? (const void*)knn_batch_handover_kernel<32>
+                : (c == 1 ? (const void*)knn_batch_handover_kernel<64>
+                          : (const void*)knn_batch_handover_kernel<128>);
+}
+
+int handover_grid(int c) {
+  int occ = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, handover_kernel(c), kThreads, 0) !=
+          cudaSuccess ||
+      occ < 1) {
+    cudaGetLastError();
+    occ = 1;
+  }
+  return num_sms() * occ;
+}
+
+cudaError_t launch_handover(const ReqDev* d_reqs, Handover* d_ho, int c, int grid, cudaStream_t s) {
+  void* args[] = {(void*)&d_reqs, (void*)&d_ho, (void*)&c};
+  return cudaLaunchKernel(handover_kernel(c), dim3((unsigned)grid), dim3((unsigned)kThreads), args,
+                          0, s);
+}
+
+// Enqueues the plan's work on stream s: the locality sorts, the persistent
+// launch of each segment, then the one-warp launches for the queries the
+// one-lane items handed over.
 cudaError_t enqueue(mknn_batch* b, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(b->d_next, 0, b->segs.size() * sizeof(int), s);
   if (e != cudaSuccess) return e;
+  if (b->d_ho) {
+    e = cudaMemsetAsync(&b->d_ho->count[0], 0, sizeof(Handover) - offsetof(Handover, count), s);
+    if (e != cudaSuccess) return e;
+  }
   for (int r = 0; r < b->nreq; ++r) {
     if (!b->perm_off[r]) continue;
     const mknn_batch_req& R = b->reqs[r];
@@ -506,8 +618,11 @@ cudaError_t enqueue(mknn_batch* b, cudaStream_t s) {
                                 (int32_t*)((char*)b->d_ws + b->perm_off[r]), s);
     if (e != cudaSuccess) return e;
   }
-  return launch_segments(b->d_reqs, b->d_items, b->d_next, b->segs, s, b->aux, b->ev_fork,
-                         b->ev_join, b->total_queries);
+  e = launch_segments(b->d_reqs, b->d_items, b->d_next, b->segs, s, b->aux, b->ev_fork,
+                      b->ev_join, b->total_queries);
+  for (int c = 0; c < 3 && e == cudaSuccess; ++c)
+    if (b->ho_class[c]) e = launch_handover(b->d_reqs, b->d_ho, c, b->ho_grid[c], s);
+  return e;
 }
 
 }  // namespace
@@ -555,7 +670,8 @@ mknn_status mknn_batch_create(const mknn_batch_req* reqs, int32_t nreq,
     }
     if (R.nq > 0 && (!R.q || !R.out_idx || !R.out_d2))
       return bfail(MKNN_EINVAL, "request " + std::to_string(r) + ": NULL device pointer");
-    const Mode chosen = choose_mode(R.k, R.cloud->n, R.cloud->hub_bucket(), plan_nq);
+    const Mode chosen =
+        choose_mode(R.k, R.cloud->n, R.cloud->hub_bucket(), plan_nq, R.cloud->d_hub_of != nullptr);
     const int lanes = o.lanes ? o.lanes : chosen.lanes;
     const int placement = o.placement ? o.placement
                                       : (o.lanes ? default_placement(R.k, lanes) : chosen.placement);
@@ -591,9 +707,14 @@ mknn_status mknn_batch_create(const mknn_batch_req* reqs, int32_t nreq,
   std::vector<Item> items;
   std::vector<int> req_k(nreq);
   for (int r = 0; r < nreq; ++r) req_k[r] = reqs[r].k;
+  int64_t ho_cap[3] = {0, 0, 0};  // queries that may be handed over, per class
   for (int r : orderq) {
     const int v = with_trees(variant_index(b->lanes[r], reqs[r].k, b->placement[r]),
-                             reqs[r].cloud->d_hub_of != nullptr);
+                             reqs[r].cloud->d_hub_of != nullptr, true);
+    if (v == kHandoverVariant || v == kHandoverVariant128) {
+      ho_cap[handover_class(reqs[r].k)] += reqs[r].nq;
+      b->ho_class[handover_class(reqs[r].k)] = true;
+    }
     const int per = item_queries(b->lanes[r], rounds);
     for (int64_t s0 = 0; s0 < reqs[r].nq; s0 += per)
       items.push_back(Item{r, (int32_t)s0, (int32_t)std::min<int64_t>(reqs[r].nq, s0 + per), v});
@@ -613,6 +734,32 @@ mknn_status mknn_batch_create(const mknn_batch_req* reqs, int32_t nreq,
   }
   for (int r = 0; r < nreq; ++r)
     if (b->perm_off[r]) rd[r].perm = (const int32_t*)((char*)b->d_ws + b->perm_off[r]);
+  if (ho_cap[0] + ho_cap[1] + ho_cap[2] > 0) {
+    Handover h{};
+    if ((e = cudaMalloc((void**)&b->d_ho, sizeof(Handover))) != cudaSuccess ||
+        (e = cudaMalloc((void**)&b->d_ho_pairs,
+                        sizeof(int2) * (size_t)(ho_cap[0] + ho_cap[1] + ho_cap[2]))) !=
+            cudaSuccess) {
+      cudaGetLastError();
+      mknn_batch* raw = b.release();
+      free_plan(raw);
+      return bfail(MKNN_ENOMEM, "device allocation for the batch plan failed");
+    }
+    int64_t at = 0;
+    for (int c = 0; c < 3; ++c) {
+      h.list[c] = b->d_ho_pairs + at;
+      at += ho_cap[c];
+    }
+    if ((e = cudaMemcpy(b->d_ho, &h, sizeof(h), cudaMemcpyHostToDevice)) != cudaSuccess) {
+      mknn_batch* raw = b.release();
+      free_plan(raw);
+      return bfail(MKNN_ECUDA, std::string("plan upload: ") + cudaGetErrorString(e));
+    }
+    for (int r = 0; r < nreq; ++r)
+      if (reqs[r].cloud->d_hub_of) rd[r].ho = b->d_ho;
+    for (int c = 0; c < 3; ++c)
+      if (b->ho_class[c]) b->ho_grid[c] = handover_grid(c);
+  }
   if ((e = cudaMemcpy(b->d_reqs, rd.data(), sizeof(ReqDev) * nreq, cudaMemcpyHostToDevice)) !=
           cudaSuccess ||
       (e = cudaMemcpy(b->d_items, items.data(), sizeof(Item) * items.size(),

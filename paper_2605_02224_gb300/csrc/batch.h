@@ -29,7 +29,18 @@ struct ReqDev {
   const int4* hub_desc;
   const float4* hub_ent;
   const float4* hub_node;
+  // the plan's hand-over lists (one-lane items on a cloud with trees), or NULL
+  struct Handover* ho;
 };
+
+// Queries a plan's one-lane items hand over to the one-warp kernel with
+// trees, by the list class of their k (one-warp lists of 32, 64, 128 keys).
+struct Handover {
+  int2* list[3];      // (request, query index) pairs
+  int32_t count[3];   // pairs appended in this run
+  int32_t taken[3];   // pairs taken by the one-warp launches
+};
+__host__ __device__ inline int handover_class(int k) { return k <= 32 ? 0 : (k <= 64 ? 1 : 2); }
 
 // Queries per request below this bound: a lane's query index plus its
 // stride within an item (at most 256 queries) then stays below 2^31 - 1.
@@ -56,10 +67,18 @@ inline int item_queries(int lanes, int rounds) { return (32 / lanes) * rounds; }
 // took 9.2 ms, of one query 3.2 ms.
 constexpr int kItemRounds = 1;
 
-// Variant indices of the one-lane shared-memory kernels (k <= 64, k <= 128).
+// Variant indices of the one-lane shared-memory kernels (k <= 64, k <= 128),
+// and their forms that hand queries meeting a list with a box tree over to
+// the one-warp kernel (a plan's requests on clouds with trees).
 constexpr int kSmemVariant = 12;
 constexpr int kSmemVariant128 = 15;
-inline bool is_smem_variant(int v) { return v == kSmemVariant || v == kSmemVariant128; }
+constexpr int kHandoverVariant = 22;
+constexpr int kHandoverVariant128 = 23;
+inline bool is_smem_variant(int v) {
+  return v == kSmemVariant || v == kSmemVariant128 || v == kHandoverVariant ||
+         v == kHandoverVariant128;
+}
+inline bool is_smem128_variant(int v) { return v == kSmemVariant128 || v == kHandoverVariant128; }
 // Variant indices of the one-warp-per-query kernels with the list in shared
 // memory: kWarpVariant32 + 0, 1, 2 for k <= 32, 64, 128.
 constexpr int kWarpVariant32 = 16;
@@ -68,12 +87,15 @@ constexpr int kWarpVariant32 = 16;
 // kTreeVariant32 + 0, 1, 2.
 constexpr int kTreeVariant32 = 19;
 // The variant a request runs: a one-warp variant turns into its tree form
-// when the request's cloud has trees. variant_index never returns the tree
-// forms (it picks the first of equal variants).
-inline int with_trees(int v, bool trees) {
-  return (trees && v >= kWarpVariant32 && v < kWarpVariant32 + 3)
-             ? v + (kTreeVariant32 - kWarpVariant32)
-             : v;
+// when the request's cloud has trees, and with `handover` (plans, not the
+// server's packs) a one-lane variant into its hand-over form. variant_index
+// never returns these forms (it picks the first of equal variants).
+inline int with_trees(int v, bool trees, bool handover = false) {
+  if (!trees) return v;
+  if (v >= kWarpVariant32 && v < kWarpVariant32 + 3) return v + (kTreeVariant32 - kWarpVariant32);
+  if (handover && v == kSmemVariant) return kHandoverVariant;
+  if (handover && v == kSmemVariant128) return kHandoverVariant128;
+  return v;
 }
 
 // Lanes per query and where the candidate list lives (2 = shared memory,

@@ -863,28 +863,6 @@ __device__ __forceinline__ bool knn_query_smem(const CloudDev& C, float qx, floa
 // lists search a power-of-two size), k above.
 __host__ __device__ __forceinline__ int list_slots(int k) { return k <= 8 ? 8 : (k <= 16 ? 16 : k); }
 
-// One query by the list kind that suits its k (the thread's column holds
-// at least list_slots(k) slots). W: flag words of the kernel's k class.
-template <int W>
-__device__ __forceinline__ void knn_query_smem_any(const CloudDev& C, float qx, float qy,
-                                                   float qz, int k, int m, uint64_t* col,
-                                                   int32_t* __restrict__ out_idx,
-                                                   float* __restrict__ out_d2, int32_t row) {
-  if constexpr (W == 1) {
-    if (k <= 8)
-      knn_query_smem<SortedList<8, 1, true>>(C, qx, qy, qz, k, m, col, 8, out_idx, out_d2, row);
-    else if (k <= 16)
-      knn_query_smem<PermList16>(C, qx, qy, qz, k, m, col, 16, out_idx, out_d2, row);
-    else
-      knn_query_smem<SortedList<32, 1, false>>(C, qx, qy, qz, k, m, col, k, out_idx, out_d2,
-                                               row);
-  } else if constexpr (W == 2) {
-    knn_query_smem<SortedList<64, 2, false>>(C, qx, qy, qz, k, m, col, k, out_idx, out_d2, row);
-  } else {
-    knn_query_smem<SortedList<128, 4, false>>(C, qx, qy, qz, k, m, col, k, out_idx, out_d2, row);
-  }
-}
-
 // ---------------------------------------------------------------------------
 // One warp per query with the candidate list N in shared memory (for large
 // k, where one list per thread would leave a few warps per SM). The list is

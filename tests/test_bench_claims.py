@@ -77,18 +77,25 @@ def test_plan_variant_table_matches_the_library():
     assert "constexpr int kWarpVariant32 = 16;" in h
     assert "constexpr int kTreeVariant32 = 19;" in h and bench._TREE_VARIANT32 == 19
     assert table[16:19] == [(32, 1, 2), (32, 2, 2), (32, 4, 2)]
-    assert table[19:22] == table[16:19] and len(table) == 22
+    assert table[19:22] == table[16:19]
+    assert "constexpr int kHandoverVariant = 22;" in h and bench._HANDOVER_VARIANT == 22
+    assert table[22:24] == [table[12], table[15]] and len(table) == 24
 
 
 def test_plan_launch_count():
     reqs = [dict(k=k, nq=nq) for k, nq in [(16, 20000), (32, 5000), (1, 100), (8, 3_000_000),
                                           (100, 9000)]]
     lanes = np.array([1, 32, 1, 1, 32])
-    # variants (1, 64) and the warp kernels (32, 1), (32, 4) in shared memory;
-    # four requests of >= 4096 queries
-    assert bench._plan_launches(lanes, reqs) == 3 + 5 * 4
+    # one-lane segments of 16 slots (k = 16) and 8 slots (k = 1, 8), and the
+    # warp kernels (32, 1), (32, 4) in shared memory; four requests of >= 4096
+    # queries
+    assert bench._plan_launches(lanes, reqs) == 4 + 5 * 4
     # registers for the 32-lane requests: (32, 1) and (32, 4) register groups
-    assert bench._plan_launches(lanes, reqs, np.array([2, 1, 2, 2, 1])) == 3 + 5 * 4
+    assert bench._plan_launches(lanes, reqs, np.array([2, 1, 2, 2, 1])) == 4 + 5 * 4
+    # one lane on clouds with box trees: the hand-over form and a one-warp
+    # launch per hand-over class (k <= 32 here)
+    reqs3 = [dict(k=4, nq=10), dict(k=16, nq=10), dict(k=4, nq=10)]
+    assert bench._plan_launches(np.array([1, 1, 1]), reqs3, None, [True, True, False]) == 3 + 1
     # both placements at k = 32: two 32-lane variants
     lanes2 = np.array([32, 32])
     reqs2 = [dict(k=32, nq=10), dict(k=32, nq=10)]

@@ -238,15 +238,17 @@ def test_box_trees_give_the_scans_rows():
                 assert np.array_equal(tree[0], other[0]) and np.array_equal(tree[1], other[1]), k
             parity.check_rows(Pr, Q, k, mk if mk is not None else 0, *tree,
                               rows=range(0, nq, 37))
-    # the persistent kernel's two one-warp forms in one plan: this cloud (with
-    # trees) and a sphere (no list reaches 4096 entries: no trees)
+    # the persistent kernels' tree forms in one plan with a sphere (no list
+    # reaches 4096 entries: no trees): one warp per query (the tree walk) and
+    # one lane per query (the hand-over to the one-warp kernel, k = 4 and 48
+    # in the first class, 100 in the last)
     S, _ = W.sphere(20000, 75)
     so = W.permutation(20000, 76)
     cs = built_cloud(S, so, "sphere20k")
     cs.upload()
     assert cs.trees() == (0, 0)
     QS = W.box_queries(3000, 77, [-1.2] * 3, [1.2] * 3)
-    for k in (4, 48):
+    for k, lanes in ((4, 32), (48, 32), (4, 1), (48, 1), (100, 1)):
         outs, reqs = [], []
         for cl, qq in ((c, Q), (cs, QS)):
             qt = torch.from_numpy(qq).cuda()
@@ -255,7 +257,7 @@ def test_box_trees_give_the_scans_rows():
             reqs.append(dict(cloud=cl.handle, q=qt, nq=len(qq), q_stride=3, k=k, m=None,
                              m_scalar=0, out_idx=oi, out_d2=od))
             outs.append((cl, qq, oi, od))
-        M.mknn_knn_batch(reqs, torch.cuda.current_stream().cuda_stream, lanes=32, placement=2)
+        M.mknn_knn_batch(reqs, torch.cuda.current_stream().cuda_stream, lanes=lanes, placement=2)
         torch.cuda.synchronize()
         for cl, qq, oi, od in outs:
             ri, rd = run_knn(cl, qq, k, None, lanes=1, placement=2)
