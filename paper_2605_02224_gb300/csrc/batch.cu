@@ -340,10 +340,15 @@ int fill_lanes(int64_t nq, int k) {
   return lanes;
 }
 
-Mode choose_mode(int k, int64_t n, int hub, int64_t nq, bool handover) {
+Mode choose_mode(int k, int64_t n, int hub, int64_t nq, bool trees) {
   const Mode t = tuned_mode(k, n, hub);
-  const int base = t.lanes ? t.lanes : heuristic_lanes(k, hub, handover);
-  int lanes = std::max(base, fill_lanes(nq, k));
+  const int fill = fill_lanes(nq, k);
+  // one lane with the hand-over only where the launch stays one lane wide
+  const int base = t.lanes ? t.lanes : heuristic_lanes(k, hub, trees && fill == 1);
+  int lanes = std::max(base, fill);
+  // widened on a cloud with box trees: the one-warp kernel, which walks them
+  // (register groups would read the long lists through)
+  if (trees && lanes > base && lanes < 32) lanes = 32;
   while (lanes < 32 && variant_index(lanes, k, 1) < 0) lanes <<= 1;  // e.g. 4 lanes hold k <= 16
   const int placement = (t.lanes && lanes == t.lanes) ? t.placement : default_placement(k, lanes);
   return Mode{lanes, placement};
@@ -486,6 +491,30 @@ std::vector<Segment> make_segments(std::vector<Item>& items, int blocks_per_sm,
   return segs;
 }
 
+// The one-warp kernel of hand-over class c and its persistent grid.
+static const void* handover_kernel(int c) {
+  return c == 0 ? (const void*)knn_batch_handover_kernel<32>
+                : (c == 1 ? (const void*)knn_batch_handover_kernel<64>
+                          : (const void*)knn_batch_handover_kernel<128>);
+}
+
+int handover_grid(int c) {
+  int occ = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, handover_kernel(c), kThreads, 0) !=
+          cudaSuccess ||
+      occ < 1) {
+    cudaGetLastError();
+    occ = 1;
+  }
+  return num_sms() * occ;
+}
+
+cudaError_t launch_handover(const ReqDev* d_reqs, Handover* d_ho, int c, int grid, cudaStream_t s) {
+  void* args[] = {(void*)&d_reqs, (void*)&d_ho, (void*)&c};
+  return cudaLaunchKernel(handover_kernel(c), dim3((unsigned)grid), dim3((unsigned)kThreads), args,
+                          0, s);
+}
+
 cudaError_t launch_segments(const ReqDev* d_reqs, const Item* d_items, int* d_next,
                             const std::vector<Segment>& segs, cudaStream_t s, cudaStream_t aux,
                             cudaEvent_t fork, cudaEvent_t join, int64_t queries) {
@@ -572,30 +601,6 @@ void free_plan(mknn_batch* b) {
   if (b->ev_join) cudaEventDestroy(b->ev_join);
   if (b->aux) cudaStreamDestroy(b->aux);
   delete b;
-}
-
-// The one-warp kernel of hand-over class c and its persistent grid.
-const void* handover_kernel(int c) {
-  return c == 0 ? (const void*)knn_batch_handover_kernel<32>
-                : (c == 1 ? (const void*)knn_batch_handover_kernel<64>
-                          : (const void*)knn_batch_handover_kernel<128>);
-}
-
-int handover_grid(int c) {
-  int occ = 1;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, handover_kernel(c), kThreads, 0) !=
-          cudaSuccess ||
-      occ < 1) {
-    cudaGetLastError();
-    occ = 1;
-  }
-  return num_sms() * occ;
-}
-
-cudaError_t launch_handover(const ReqDev* d_reqs, Handover* d_ho, int c, int grid, cudaStream_t s) {
-  void* args[] = {(void*)&d_reqs, (void*)&d_ho, (void*)&c};
-  return cudaLaunchKernel(handover_kernel(c), dim3((unsigned)grid), dim3((unsigned)kThreads), args,
-                          0, s);
 }
 
 // Enqueues the plan's work on stream s: the locality sorts, the persistent

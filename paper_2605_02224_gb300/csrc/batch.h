@@ -41,6 +41,10 @@ struct Handover {
   int32_t taken[3];   // pairs taken by the one-warp launches
 };
 __host__ __device__ inline int handover_class(int k) { return k <= 32 ? 0 : (k <= 64 ? 1 : 2); }
+// The persistent grid of the one-warp launch that drains hand-over class c,
+// and that launch (after the segments whose items hand queries over).
+int handover_grid(int c);
+cudaError_t launch_handover(const ReqDev* d_reqs, Handover* d_ho, int c, int grid, cudaStream_t s);
 
 // Queries per request below this bound: a lane's query index plus its
 // stride within an item (at most 256 queries) then stays below 2^31 - 1.
@@ -153,10 +157,11 @@ void set_tuned_mode(int k, int64_t n, int hub, Mode m);
 // Mode for a launch of nq queries: the tuned (or default) lanes for
 // (k, n, hub), widened for batches too small to fill the GPU one query per
 // thread, and the tuned placement (or the default for those lanes).
-// handover: the launch hands queries that meet a list with a box tree over
-// to the one-warp kernel (mknn_knn_ex on a cloud with trees), which makes
-// one lane the better default for small k.
-Mode choose_mode(int k, int64_t n, int hub, int64_t nq, bool handover = false);
+// trees: the cloud has box trees and the launch can use them (the one-warp
+// kernel walks them; one lane hands queries that meet them over to it):
+// then one lane is the default for small k when the launch stays one lane
+// wide, and a launch widened for its size goes to 32 lanes.
+Mode choose_mode(int k, int64_t n, int hub, int64_t nq, bool trees = false);
 // The smallest lane width that fills the GPU with nq queries of this k.
 int fill_lanes(int64_t nq, int k);
 

@@ -135,6 +135,12 @@ size_t items_bytes(int64_t nq_total, size_t nreq) {
   return al(sizeof(Item) * ((size_t)nq_total + 2 * nreq + 64));
 }
 
+// Room for a pack's hand-over: the lists' header and a (request, query)
+// pair per query (one-lane items on clouds with box trees).
+size_t handover_bytes(int64_t nq_total) {
+  return al(sizeof(Handover)) + al(sizeof(int2) * (size_t)nq_total);
+}
+
 constexpr size_t kPackFixed = kSortHistBytes + 1024;  // histogram, tile totals, counter
 
 }  // namespace
@@ -248,7 +254,7 @@ void mknn_server::launch(Slot& sl, std::vector<uint64_t>& tickets, size_t off, s
     if (e == cudaSuccess) e = cudaMemcpyAsync(di, dbase + R.idx_off, nk, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(dd, dbase + R.d2_off, nk, cudaMemcpyDeviceToHost, s);
   } else {
-    // pack layout: [counter][histogram][ReqDev x n][Item x m][per request data]
+    // pack layout: [counter][histogram][ReqDev x n][Item x m][hand-over][per request data]
     int* d_next = (int*)dbase;
     void* d_hist = dbase + 256;
     const size_t reqs_off = 256 + kSortHistBytes;
@@ -262,10 +268,14 @@ void mknn_server::launch(Slot& sl, std::vector<uint64_t>& tickets, size_t off, s
     for (int i = 0; i < nreq; ++i) {
       const mknn_request& q = recs[tickets[i] - 1].r;
       const mknn_cloud* c = clouds[q.cloud];
-      const Mode chosen = choose_mode(q.k, c->n, c->hub_bucket(), pack_nq);
+      const Mode chosen = choose_mode(q.k, c->n, c->hub_bucket(), pack_nq, c->d_hub_of != nullptr);
       lanes[i] = o.lanes ? o.lanes : chosen.lanes;
       placement[i] = o.lanes ? default_placement(q.k, lanes[i]) : chosen.placement;
     }
+    const size_t ho_off = reqs_off + al(sizeof(ReqDev) * nreq) + items_bytes(pack_nq, nreq);
+    Handover* d_ho = (Handover*)(dbase + ho_off);
+    int2* d_pairs = (int2*)(dbase + ho_off + al(sizeof(Handover)));
+    int64_t ho_cap[3] = {0, 0, 0};
     for (int i = 0; i < nreq; ++i) {
       ReqRec& R = recs[tickets[i] - 1];
       const mknn_request& q = R.r;
@@ -286,7 +296,12 @@ void mknn_server::launch(Slot& sl, std::vector<uint64_t>& tickets, size_t off, s
                      q.m ? q.m : (int32_t)c->n, (const float4*)cd.ent, cd.hub_of,
                      (const int4*)cd.hub_desc, (const float4*)cd.hub_ent,
                      (const float4*)cd.hub_node};
-      const int v = with_trees(variant_index(lanes[i], q.k, placement[i]), cd.hub_of != nullptr);
+      const int v =
+          with_trees(variant_index(lanes[i], q.k, placement[i]), cd.hub_of != nullptr, true);
+      if (v == kHandoverVariant || v == kHandoverVariant128) {
+        ho_cap[handover_class(q.k)] += q.nq;
+        rd[i].ho = d_ho;
+      }
       const int per = item_queries(lanes[i], kItemRounds);
       req_k[i] = q.k;
       for (int64_t b0 = 0; b0 < q.nq; b0 += per)
@@ -301,6 +316,18 @@ void mknn_server::launch(Slot& sl, std::vector<uint64_t>& tickets, size_t off, s
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(dbase + reqs_off, hbase + reqs_off,
                           items_off - reqs_off + sizeof(Item) * ni, cudaMemcpyHostToDevice, s);
+    const bool handover = ho_cap[0] + ho_cap[1] + ho_cap[2] > 0;
+    if (handover) {  // the lists' header, counters at zero, through the pinned mirror
+      Handover h{};
+      int64_t at = 0;
+      for (int c = 0; c < 3; ++c) {
+        h.list[c] = d_pairs + at;
+        at += ho_cap[c];
+      }
+      std::memcpy(hbase + ho_off, &h, sizeof(h));
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_ho, hbase + ho_off, sizeof(h), cudaMemcpyHostToDevice, s);
+    }
     if (e == cudaSuccess) e = cudaEventRecord(sl.t_h2d, s);
     // the locality sort of each request, then the pack's kernels
     for (int i = 0; i < nreq && e == cudaSuccess; ++i) {
@@ -316,6 +343,10 @@ void mknn_server::launch(Slot& sl, std::vector<uint64_t>& tickets, size_t off, s
     if (e == cudaSuccess)
       e = launch_segments((const ReqDev*)(dbase + reqs_off), (const Item*)(dbase + items_off),
                           d_next, segs, s, sl.aux, sl.fork, sl.join, pack_nq);
+    // the handed-over queries, after every segment
+    for (int c = 0; c < 3 && handover && e == cudaSuccess; ++c)
+      if (ho_cap[c] > 0)
+        e = launch_handover((const ReqDev*)(dbase + reqs_off), d_ho, c, handover_grid(c), s);
     if (e == cudaSuccess) e = cudaEventRecord(sl.t_kern, s);
     for (int i = 0; i < nreq && e == cudaSuccess; ++i) {
       ReqRec& R = recs[tickets[i] - 1];
@@ -359,7 +390,8 @@ void mknn_server::run() {
       const ReqRec& R = recs[t - 1];
       const size_t rb = request_bytes(R.r.nq, R.r.k);
       const size_t meta = o.plain ? 0 : al(sizeof(ReqDev) * (take.size() + 1)) +
-                                            items_bytes(nq_total + R.r.nq, take.size() + 1);
+                                            items_bytes(nq_total + R.r.nq, take.size() + 1) +
+                                            handover_bytes(nq_total + R.r.nq);
       if (!take.empty() && (bytes + rb + meta > room || nq_total + R.r.nq > o.max_batch_queries))
         break;
       if (take.empty() && bytes + rb + meta > room) break;  // wait for memory
@@ -371,7 +403,7 @@ void mknn_server::run() {
     if (take.empty()) continue;
     const size_t meta = o.plain ? kSortHistBytes + 256
                                 : al(sizeof(ReqDev) * take.size()) +
-                                      items_bytes(nq_total, take.size());
+                                      items_bytes(nq_total, take.size()) + handover_bytes(nq_total);
     bytes += meta;
     size_t off = 0;
     if (!arena.alloc(bytes, &off)) continue;
@@ -389,7 +421,7 @@ void mknn_server::run() {
       R.d2_off = c;
     } else {
       size_t c = 256 + kSortHistBytes + al(sizeof(ReqDev) * take.size()) +
-                 items_bytes(nq_total, take.size());
+                 items_bytes(nq_total, take.size()) + handover_bytes(nq_total);
       for (uint64_t t : take) {
         ReqRec& R = recs[t - 1];
         const int64_t nq = R.r.nq;

@@ -184,3 +184,52 @@ def test_drain_times_out_then_completes(torch, resident):
     M.mknn_server_drain(srv, 120.0)
     assert M.mknn_server_poll(srv, t) == 1
     M.mknn_server_destroy(srv, 30.0)
+
+
+def test_served_rows_on_a_cloud_with_box_trees(torch):
+    """A resident cloud with box trees (400k-site planar patches, lists of up
+    to ~33k entries) beside one without: the batched server's packs hand the
+    one-lane queries that meet a list with a tree over to the one-warp kernel
+    and walk the trees for one-warp requests; every served row equals the
+    same request run alone through mknn_knn."""
+    from tests.gpu_util import built_cloud
+    n = 400_000
+    P, _ = W.patches4(n, 21200)
+    c = built_cloud(P, W.permutation(n, 21201), "patches400k")
+    c.upload()
+    assert c.trees()[0] > 0
+    S, _ = W.sphere(20000, 75)
+    cs = built_cloud(S, W.permutation(20000, 76), "sphere20k")
+    cs.upload()
+    Pr = P[W.permutation(n, 21201)]
+    _, rowp, _ = c.table()
+    hubs = np.argsort(-np.diff(rowp), kind="stable")[:200]
+    # packs of up to 2^20 queries, so that k <= 8 requests stay one lane wide
+    # (smaller packs widen them to 32 lanes)
+    srv = M.mknn_server_create(slots=3, plain=0, mem_budget=1 << 30, max_batch_queries=1 << 20)
+    ids = [M.mknn_server_add_cloud(srv, h.handle) for h in (c, cs)]
+    jobs = []
+    for j, (k, m) in enumerate([(1, 0), (4, 0), (8, n // 3), (16, 0), (48, 0), (100, n // 2),
+                                (4, 0), (32, 0)]):
+        nq = 30000 + 1000 * j
+        near = Pr[hubs[np.arange(nq) % len(hubs)]] + \
+            1e-3 * W.normal(80 + j, 1, 3 * nq).reshape(-1, 3)
+        Q = np.concatenate([near[: nq // 2],
+                            W.box_queries(nq - nq // 2, 90 + j, [0.0] * 3, [1.0] * 3)])
+        Q = np.ascontiguousarray(Q, np.float32)
+        which = 0 if j % 4 else 1
+        oi = np.empty((nq, k), np.int32)
+        od = np.empty((nq, k), np.float32)
+        mm = m if which == 0 else 0
+        t = M.mknn_server_submit(srv, ids[which], Q, k, mm, oi, od)
+        jobs.append(((c, cs)[which], Q, k, mm, oi, od, t))
+    M.mknn_server_drain(srv, 120.0)
+    st = M.mknn_server_stats(srv)
+    assert st["completed"] == len(jobs) and st["failed"] == 0
+    for cl, Q, k, mm, oi, od, _ in jobs:
+        ri, rd = cl.knn(torch.from_numpy(Q).cuda(), k, mm or None)
+        torch.cuda.synchronize()
+        assert np.array_equal(oi, ri.cpu().numpy()) and np.array_equal(od, rd.cpu().numpy()), k
+    M.mknn_server_destroy(srv, 10.0)
+    cs.close()
+    c.close()
