@@ -223,7 +223,7 @@ __global__ void __launch_bounds__(kThreads) knn_batch_warp_kernel(const ReqDev* 
                                                                   int* __restrict__ next,
                                                                   int kcap) {
   (void)kcap;
-  __shared__ uint64_t lists[kThreads / 32][kWarpListWords(KC)];
+  __shared__ uint64_t lists[kThreads / 32][TREES ? kWarpListWords(KC) : KC];
   const int warp = (int)(threadIdx.x >> 5);
   const uint32_t lane = threadIdx.x & 31u;
   for (;;) {

@@ -998,54 +998,64 @@ __device__ __forceinline__ float box_sqd32(float qx, float qy, float qz, float4 
   return d;
 }
 
-// Depth-first walk of tree D. The children of a node are tested one per
-// lane with keep(low, high) and the kept ones are entered in order; each is
-// tested again when entered, since the bounds tighten as chunks are
-// handled. A kept chunk (level 0) goes to leaf(chunk). Every decision is
-// the same in all lanes, so the warp stays converged. stack: 2 x
-// kHubMaxLevels words of the warp's shared memory.
-template <class Keep, class Leaf>
+// Depth-first walk of tree D. The children of a node are rated one per lane
+// with rate(low, high): a priority below 0xffffffff for a child that may
+// hold an entry of interest (the smaller, the sooner it is entered), else
+// 0xffffffff. The kept children of each level wait in a bit mask, their
+// priorities in the warp's shared memory; the one with the smallest
+// priority is entered next if still(priority) holds then (the bounds
+// tighten as chunks are handled), and a kept chunk (level 0) goes to
+// leaf(chunk). Every decision is the same in all lanes, so the warp stays
+// converged. stack: kHubStackWords 32-bit words of the warp's shared memory.
+template <class Rate, class Still, class Leaf>
 __device__ __forceinline__ void hub_walk(const CloudDev& C, int4 D, int lane, uint32_t* stack,
-                                         Keep&& keep, Leaf&& leaf) {
+                                         Rate&& rate, Still&& still, Leaf&& leaf) {
   const int len = D.y, node0 = D.z, top = D.w - 1;
-  // per level: the children not entered yet (pend) and the index of their
-  // first (first); every lane writes the same values
+  // per level: the children not entered yet (pend), the index of their
+  // first (first), and each child's priority (prio, one per lane)
   uint32_t* pend = stack;
   uint32_t* first = stack + kHubMaxLevels;
+  uint32_t* prio = stack + 2 * kHubMaxLevels;
   int l = top, off, cnt;
   hub_level_of(len, l, off, cnt);
-  bool kept = false;
+  uint32_t pr = 0xffffffffu;
   if (lane < cnt) {
     const int j = node0 + off + lane;
-    kept = keep(__ldg(C.hub_node + 2 * j), __ldg(C.hub_node + 2 * j + 1));
+    pr = rate(__ldg(C.hub_node + 2 * j), __ldg(C.hub_node + 2 * j + 1));
   }
-  pend[l] = __ballot_sync(0xffffffffu, kept);
+  prio[32 * l + lane] = pr;
+  pend[l] = __ballot_sync(0xffffffffu, pr != 0xffffffffu);
   first[l] = 0;
+  __syncwarp();
   for (;;) {
     const uint32_t pm = pend[l];
     if (pm == 0u) {
       if (++l > top) break;
       continue;
     }
-    const int node = (int)first[l] + __ffs((int)pm) - 1;
-    pend[l] = pm & (pm - 1u);
-    hub_level_of(len, l, off, cnt);
-    const int j = node0 + off + node;
-    if (!keep(__ldg(C.hub_node + 2 * j), __ldg(C.hub_node + 2 * j + 1))) continue;
+    const uint32_t mine = ((pm >> lane) & 1u) ? prio[32 * l + lane] : 0xffffffffu;
+    const uint32_t low = __reduce_min_sync(0xffffffffu, mine);
+    const int c = __ffs((int)__ballot_sync(0xffffffffu, mine == low)) - 1;
+    pend[l] = pm & ~(1u << c);
+    const int node = (int)first[l] + c;
+    if (!still(low)) continue;
     if (l == 0) {
       leaf(node);
       continue;
     }
     --l;
     hub_level_of(len, l, off, cnt);
-    const int c = 32 * node + lane;
-    kept = false;
-    if (c < cnt) {
-      const int jc = node0 + off + c;
-      kept = keep(__ldg(C.hub_node + 2 * jc), __ldg(C.hub_node + 2 * jc + 1));
+    const int ch = 32 * node + lane;
+    pr = 0xffffffffu;
+    if (ch < cnt) {
+      const int jc = node0 + off + ch;
+      pr = rate(__ldg(C.hub_node + 2 * jc), __ldg(C.hub_node + 2 * jc + 1));
     }
-    pend[l] = __ballot_sync(0xffffffffu, kept);
+    __syncwarp();  // every lane has read this level's old priorities
+    prio[32 * l + lane] = pr;
+    pend[l] = __ballot_sync(0xffffffffu, pr != 0xffffffffu);
     first[l] = (uint32_t)(32 * node);
+    __syncwarp();
   }
 }
 
@@ -1066,8 +1076,10 @@ __device__ __forceinline__ int hub_first_closer(const CloudDev& C, int hub, floa
       C, D, lane, stack,
       [&](float4 lo, float4 hi) {
         const int r = __float_as_int(lo.w);
-        return r < m && r < best && !(box_sqd32(qx, qy, qz, lo, hi) > reach);
+        return (r < m && r < best && !(box_sqd32(qx, qy, qz, lo, hi) > reach)) ? (uint32_t)r
+                                                                               : 0xffffffffu;
       },
+      [&](uint32_t r) { return (int)r < best; },
       [&](int chunk) {
         const float4 ps = __ldg(C.hub_ent + D.x + 32 * chunk + lane);
         const int s = __float_as_int(ps.w);  // pads: 0x7fffffff, never below m
@@ -1098,8 +1110,10 @@ __device__ __forceinline__ void hub_offer(const CloudDev& C, int hub, float qx, 
       C, D, lane, stack,
       [&](float4 lo, float4 hi) {
         const float wd = __uint_as_float((uint32_t)(N.worst >> 32));
-        return __float_as_int(lo.w) < m && !(box_sqd32(qx, qy, qz, lo, hi) > wd);
+        const float bd = box_sqd32(qx, qy, qz, lo, hi);
+        return (__float_as_int(lo.w) < m && !(bd > wd)) ? __float_as_uint(bd) : 0xffffffffu;
       },
+      [&](uint32_t d) { return !(__uint_as_float(d) > __uint_as_float((uint32_t)(N.worst >> 32))); },
       [&](int chunk) {
         const float4 ps = __ldg(C.hub_ent + D.x + 32 * chunk + lane);
         const int s = __float_as_int(ps.w);
@@ -1116,8 +1130,11 @@ __device__ __forceinline__ void hub_offer(const CloudDev& C, int hub, float qx, 
       });
 }
 
+// 32-bit words of a warp's tree-walk stack: per level a mask, a first
+// index and 32 priorities.
+constexpr int kHubStackWords = 34 * kHubMaxLevels;
 // 64-bit words of shared memory for one warp of knn_query_warp<KC>.
-__host__ __device__ constexpr int kWarpListWords(int kc) { return kc + kHubMaxLevels; }
+__host__ __device__ constexpr int kWarpListWords(int kc) { return kc + kHubStackWords / 2; }
 
 // One query by one warp (every lane calls it with the same query). With
 // TREES (a cloud whose hub_of is not NULL) a list with a box tree is

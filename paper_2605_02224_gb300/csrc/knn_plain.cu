@@ -230,7 +230,7 @@ __global__ void __launch_bounds__(kThreads) knn_plain_warp_kernel(
     const int32_t* __restrict__ mq, int m_scalar, const int32_t* __restrict__ perm,
     int32_t* __restrict__ out_idx, float* __restrict__ out_d2, int32_t* __restrict__ err,
     const int32_t* __restrict__ count) {
-  __shared__ uint64_t lists[kThreads / 32][kWarpListWords(KC)];
+  __shared__ uint64_t lists[kThreads / 32][TREES ? kWarpListWords(KC) : KC];
   if (count) nq = min(nq, (int64_t)__ldg(count));  // queries a deferring launch handed over
   const int warp = (int)(threadIdx.x >> 5), lane = (int)(threadIdx.x & 31u);
   const int64_t nw = (int64_t)gridDim.x * (kThreads / 32);
