@@ -928,13 +928,57 @@ struct WarpList {
     }
     return r;
   }
-  // is key c in the list? (called by any subset of lanes)
-  __device__ __forceinline__ bool contains(uint64_t c) const {
-    int pos = 0;
+  // is key c in the list? pos: the number of keys below c (called by any
+  // subset of lanes)
+  __device__ __forceinline__ bool contains(uint64_t c, int& pos) const {
+    pos = 0;
 #pragma unroll
     for (int step = KC / 2; step >= 1; step >>= 1)
       if (L[pos + step - 1] < c) pos += step;
     return L[pos] == c;
+  }
+  // Inserts key c, not in the list and below the k-th key, at position pos
+  // (the number of keys below it; the same in every lane; called by the
+  // whole warp).
+  __device__ __forceinline__ void insert_at(uint64_t c, int pos, int k, int lane) {
+    uint64_t prev[J];
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+      const int p = lane + 32 * j;
+      prev[j] = (p > pos && p < k) ? L[p - 1] : 0ull;
+    }
+    __syncwarp();  // every lane has read its previous keys
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+      const int p = lane + 32 * j;
+      if (p < k) {
+        if (p > pos)
+          L[p] = prev[j];
+        else if (p == pos)
+          L[p] = c;
+      }
+    }
+    __syncwarp();
+    open_flag(pos);
+    if (cnt < k) cnt++;
+    if (cnt == k) worst = L[k - 1];
+  }
+  // Offers the lanes' keys with `fresh` set (below the k-th key, not in the
+  // list; positions from contains) one after another, lowest lane first:
+  // each one still below the k-th key goes in at its position, and the
+  // positions of the keys after it that are larger move up by one.
+  __device__ __forceinline__ void offer(bool fresh, uint64_t key, int pos, int k, int lane) {
+    uint32_t b = __ballot_sync(0xffffffffu, fresh);
+    while (b) {
+      const int j = __ffs((int)b) - 1;
+      b &= b - 1;
+      const uint64_t c = __shfl_sync(0xffffffffu, key, j);
+      const int at = __shfl_sync(0xffffffffu, pos, j);
+      if (c < worst) {
+        insert_at(c, at, k, lane);
+        if (key > c) ++pos;
+      }
+    }
   }
   // Inserts key c (the same in every lane; called by the whole warp) unless
   // present; keeps k entries.
@@ -1121,14 +1165,9 @@ __device__ __forceinline__ void hub_offer(const CloudDev& C, int hub, float qx, 
         const int s = __float_as_int(ps.w);
         const float d = sqd32(qx, qy, qz, ps);
         const uint64_t key = pack_key(d, (uint32_t)s);
-        const bool fresh = s < m && key < N.worst && !N.contains(key);
-        uint32_t b = __ballot_sync(0xffffffffu, fresh);
-        while (b) {
-          const int j = __ffs((int)b) - 1;
-          b &= b - 1;
-          const uint64_t c = __shfl_sync(0xffffffffu, key, j);
-          if (c < N.worst) N.insert(c, k, lane);
-        }
+        int pos = 0;
+        const bool fresh = s < m && key < N.worst && !N.contains(key, pos);
+        N.offer(fresh, key, pos, k, lane);
       });
 }
 
@@ -1212,14 +1251,9 @@ __device__ __forceinline__ void knn_query_warp(const CloudDev& C, float qx, floa
         }
         if (row_done) cur = -1;
       } else {
-        const bool fresh = inr && key < N.worst && !N.contains(key);
-        uint32_t b = __ballot_sync(0xffffffffu, fresh);
-        while (b) {
-          const int j = __ffs((int)b) - 1;
-          b &= b - 1;
-          const uint64_t c = __shfl_sync(0xffffffffu, key, j);
-          if (c < N.worst) N.insert(c, k, lane);
-        }
+        int pos = 0;
+        const bool fresh = inr && key < N.worst && !N.contains(key, pos);
+        N.offer(fresh, key, pos, k, lane);
       }
       if (!row_done) {
         base += 32;
