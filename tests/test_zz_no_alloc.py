@@ -90,6 +90,27 @@ def test_noalloc_at_its_limit_and_on_small_batches(torch_cuda):
     hub.close()
 
 
+def test_noalloc_on_a_cloud_with_box_trees(torch_cuda):
+    """On a cloud with box trees the call takes the one-warp kernel, which
+    walks them (it has no scratch for the one-lane hand-over); rows equal
+    mknn_knn's, for small and large batches."""
+    torch = torch_cuda
+    from tests.gpu_util import built_cloud
+    n = 400_000
+    P, _ = W.patches4(n, 21200)
+    c = built_cloud(P, W.permutation(n, 21201), "patches400k")
+    c.upload()
+    assert c.trees()[0] > 0
+    lo, hi = W.padded_box(P)
+    for nq, k in ((100, 4), (5000, 8), (300_000, 4), (20_000, 48)):
+        Q = W.box_queries(nq, 80 + nq % 97, lo, hi)
+        ref_i, ref_d = _run(torch, M.mknn_knn, c, Q, k, None)
+        got_i, got_d = _run(torch, M.mknn_knn_noalloc, c, Q, k, None)
+        assert np.array_equal(got_i, ref_i) and np.array_equal(got_d, ref_d), (nq, k)
+    assert c.check() == 0
+    c.close()
+
+
 def test_noalloc_rejects_batches_above_its_limit(torch_cuda):
     torch = torch_cuda
     wl = W.small_sphere(nq=1)
